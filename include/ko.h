@@ -1,0 +1,163 @@
+/*
+ * ko.h -- C ABI of libko, a GB300 (sm_103a) engine that scores kernel launch
+ * orders by makespan over the whole permutation space of a set of independent
+ * kernels, each launched on its own stream.
+ *
+ * Method: Li, Narayana, El-Ghazawi, "Reordering GPU Kernel Launches to Enable
+ * Efficient Concurrent Execution" (arXiv 1511.07983).
+ *   - GPU / kernel parameters: Table 1.
+ *   - Dispatch rule: Sec. 2 -- all thread blocks of the earliest-issued kernel
+ *     are placed before any block of the next one, round-robin over SMs, until
+ *     one of the four SM limits (registers, shared memory, warps, blocks) is
+ *     met; blocks that do not fit wait for a later execution round.
+ *   - Compute/memory balance R_B: Sec. 4.
+ *   - Launch-order heuristic: Algorithm 1 (ScoreGen, ProfileCombine).
+ *   - Evaluation over all permutations, percentile rank, speedup over worst,
+ *     deviation from optimal: Sec. 6 and Table 3.
+ *
+ * The paper measures each order on hardware; this library replaces the
+ * measurement with an integer discrete-event model.  A block of kernel i that
+ * starts in a dispatch burst on an SM whose resident blocks (after the burst)
+ * sum to SumC compute and SumM memory cycles runs for
+ *     d = max( ceil(c_i * max(SumC, Ccap) / Ccap), ceil(m_i * max(SumM, Mcap) / Mcap) )
+ * cycles, so R_B = Ccap / Mcap.  The round-robin pointer persists across
+ * bursts; the queue is strict FIFO (no overtaking); all blocks ending at the
+ * same time are released before the next burst.
+ *
+ * Conventions
+ *   - Every call returns a ko_status (0 = KO_OK, negative = error) unless
+ *     stated otherwise; ko_last_error() returns the last error of the calling
+ *     thread and ko_status_str() names it.
+ *   - A handle (ko_gpu) owns copies of all its inputs and the device scratch
+ *     it allocates; output buffers belong to the caller.  One handle per host
+ *     thread; distinct handles are independent.
+ *   - Pointer arguments documented "host or device" are classified with
+ *     cudaPointerGetAttributes; host buffers are staged through the handle's
+ *     device scratch and copied back before the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     return host results synchronise that stream before returning.
+ *   - Lehmer indices are lexicographic: index 0 is the order 0,1,...,N-1 and
+ *     index N!-1 is N-1,...,0.
+ */
+#ifndef KO_H
+#define KO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ko_status;
+
+#define KO_OK 0
+#define KO_ERR_ARG (-1)       /* NULL handle, non-positive or out-of-range field, N > 24 */
+#define KO_ERR_NOFIT (-2)     /* a block of some kernel exceeds an empty SM */
+#define KO_ERR_TOO_LARGE (-3) /* exhaustive scoring asked for N > 12 */
+#define KO_ERR_OVERFLOW (-4)  /* makespan upper bound does not fit 62 bits */
+#define KO_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define KO_ERR_TIMEOUT (-6)   /* a bounded device wait gave up */
+#define KO_ERR_STATE (-7)     /* call not valid in the handle's current state */
+#define KO_ERR_NOMEM (-8)     /* device or host allocation failed */
+
+/* Limits accepted by ko_create_gpu / ko_add_kernel. */
+#define KO_MAX_KERNELS 24
+#define KO_MAX_EXHAUSTIVE 12
+#define KO_MAX_SM 1024
+#define KO_MAX_BLK_SM 32
+#define KO_MAX_CYCLES (1 << 24)
+
+typedef struct ko_gpu ko_gpu;
+
+/* Exhaustive statistics of one set (Table 3 columns, Sec. 6).
+ *   min / max            best and worst makespan over all N! orders
+ *   makespan             makespan of the ranked order
+ *   n_better/equal/worse orders strictly faster / equal / strictly slower
+ *   percentile           100 * (n_worse + n_equal) / N!   (share of orders that
+ *                        are at least as slow as the ranked one)
+ *   percentile_strict    100 * n_worse / N!
+ *   speedup_over_worst   max / makespan
+ *   deviation_from_optimal (makespan - min) / min                          */
+typedef struct {
+    int64_t min, max, makespan;
+    uint64_t n_total, n_better, n_equal, n_worse;
+    double percentile, percentile_strict, speedup_over_worst, deviation_from_optimal;
+} ko_rank;
+
+/* Create a simulated GPU (Table 1, first three rows): number of SMs and the
+ * per-SM register, shared-memory (bytes), warp and block limits.  Ranges:
+ * n_sm 1..1024, n_blk_sm 1..32, the others 1..2^24.  Capacities default to
+ * Ccap = Mcap = 32768 (R_B = 1).  Returns NULL on a bad argument
+ * (ko_last_error() says why).  The handle must be released with
+ * ko_destroy_gpu. */
+ko_gpu *ko_create_gpu(int32_t n_sm, int32_t n_reg_sm, int32_t n_shm_sm, int32_t n_warp_sm,
+                      int32_t n_blk_sm);
+
+/* Per-SM compute and memory capacities (cycles of demand served per cycle);
+ * R_B = c_cap / m_cap (Sec. 4).  Both in 1..2^30.  KO_ERR_STATE after the
+ * first evaluation. */
+ko_status ko_set_capacity(ko_gpu *g, int64_t c_cap, int64_t m_cap);
+
+/* Append kernel i (Table 1, last three rows), all quantities per thread
+ * block: n_reg_i = registers of one block (regs/thread x threads), n_shm_i =
+ * shared-memory bytes of one block, n_warp_i = warps of one block,
+ * n_tblk_i = number of blocks, c_i / m_i = compute / memory cycles one block
+ * needs when running alone (R_i = c_i / m_i).  n_reg_i, n_warp_i, n_tblk_i,
+ * c_i, m_i must be >= 1 (n_tblk_i <= 2^20, c_i and m_i <= 2^24), n_shm_i >= 0.
+ * Returns the kernel id (0, 1, ...) or a negative ko_status; KO_ERR_NOFIT if
+ * one block cannot fit an empty SM, KO_ERR_STATE after the first evaluation. */
+int32_t ko_add_kernel(ko_gpu *g, int32_t n_reg_i, int32_t n_shm_i, int32_t n_warp_i,
+                      int32_t n_tblk_i, int64_t c_i, int64_t m_i);
+
+/* Number of kernels added so far (>= 0), or KO_ERR_ARG for a NULL handle. */
+int32_t ko_num_kernels(const ko_gpu *g);
+
+/* Work/capacity lower bound and serial upper bound on the makespan of any
+ * order.  lb = max(longest alone-duration, per-limit area bounds); ub = sum of
+ * all blocks' durations with SumC, SumM at N_blk_SM times the largest c, m.
+ * Host-only; KO_ERR_OVERFLOW if ub needs more than 62 bits. */
+ko_status ko_bounds(ko_gpu *g, int64_t *lb, int64_t *ub);
+
+/* Algorithm 1 (ScoreGen / ProfileCombine, execution rounds), run on the host.
+ * Writes N kernel ids to order_out (host memory).  Resource terms use each
+ * kernel's per-SM footprint ceil(N_tblk / N_SM) x (regs, smem, warps, 1);
+ * R_i = c_i / m_i, R_B = Ccap / Mcap, R_comb = sum(N_tblk c) / sum(N_tblk m). */
+ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out);
+
+/* Makespans of n launch orders, written to makespan_out[n] (host or device).
+ * Exactly one of idx / orders is non-NULL:
+ *   idx     n Lehmer indices in [0, N!)   (N <= 20), host or device;
+ *   orders  n x N kernel ids, row-major, each row a permutation, host or device.
+ * Rows are not checked for being permutations on the device; a row with an
+ * id outside [0, N) yields makespan -1.  Asynchronous on `stream` when every
+ * pointer is a device pointer; otherwise synchronises before returning. */
+ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
+                         int64_t *makespan_out, void *stream);
+
+/* Exhaustive scoring of all N! orders (N <= 12, else KO_ERR_TOO_LARGE) and the
+ * rank of one order among them.  `order` (host, N ids) is ranked; NULL ranks
+ * the Algorithm 1 order.  If hist != NULL (host or device, nbins >= 1
+ * entries) it receives the histogram with
+ *     bin = floor((M - min) * nbins / (max - min + 1)).
+ * Synchronises `stream`; `out` is host memory. */
+ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t *hist,
+                        int32_t nbins, void *stream);
+
+/* Makespans of all N! orders in Lehmer-index order into makespans_out[N!]
+ * (device memory), N <= 12.  Asynchronous on `stream`. */
+ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
+
+/* Release the handle and its device scratch.  NULL is ignored. */
+void ko_destroy_gpu(ko_gpu *g);
+
+/* Name of a status code (static string). */
+const char *ko_status_str(ko_status s);
+
+/* Last error recorded on the calling thread (KO_OK if none). */
+ko_status ko_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KO_H */

@@ -23,6 +23,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 import threading
 
@@ -30,7 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ko_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+_BUILD = os.path.join(_HERE, "_build", platform.machine())
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None

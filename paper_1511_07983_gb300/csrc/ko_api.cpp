@@ -1,0 +1,414 @@
+// libko C ABI: handle management, argument validation, staging of host
+// buffers, and dispatch to the simulator kernels.  See include/ko.h.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "ko_internal.h"
+#include "ko_fast.h"
+
+namespace {
+
+thread_local ko_status t_last_error = KO_OK;
+
+ko_status fail(ko_status s)
+{
+    t_last_error = s;
+    return s;
+}
+
+ko_status ok()
+{
+    t_last_error = KO_OK;
+    return KO_OK;
+}
+
+constexpr size_t kSimpleScratchBudget = size_t(1) << 30;  // bytes for the simple simulator slabs
+constexpr int64_t kFactorial[21] = {1LL, 1LL, 2LL, 6LL, 24LL, 120LL, 720LL, 5040LL, 40320LL,
+                                    362880LL, 3628800LL, 39916800LL, 479001600LL, 6227020800LL,
+                                    87178291200LL, 1307674368000LL, 20922789888000LL,
+                                    355687428096000LL, 6402373705728000LL, 121645100408832000LL,
+                                    2432902008176640000LL};
+
+int log2_exact(int64_t v)
+{
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int s = 0;
+    while ((int64_t(1) << s) != v) s++;
+    return s;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct ko_gpu {
+    KoSet h{};
+    bool frozen = false;       // kernels / capacities fixed after the first evaluation
+    KoSet *d_set = nullptr;
+    KoAccum *d_acc = nullptr;
+    void *scratch = nullptr;   // simple-simulator slabs
+    size_t scratch_bytes = 0;
+    int64_t *d_ms = nullptr;   // makespan buffer
+    size_t ms_cap = 0;
+    void *d_stage = nullptr;   // staging for host inputs
+    size_t stage_cap = 0;
+    unsigned long long *d_hist = nullptr;
+    int hist_cap = 0;
+    KoFastState fast{};        // run-length simulator state (work list, overflow list)
+
+    ~ko_gpu()
+    {
+        cudaFree(d_set); cudaFree(d_acc); cudaFree(scratch); cudaFree(d_ms); cudaFree(d_stage);
+        cudaFree(d_hist);
+        ko_fast_release(&fast);
+    }
+};
+
+namespace {
+
+ko_status grow(void **p, size_t *cap, size_t need)
+{
+    if (*cap >= need) return KO_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return KO_ERR_NOMEM;
+    }
+    *cap = need;
+    return KO_OK;
+}
+
+// Upload the set (with ref_makespan) and make sure the accumulator exists.
+ko_status prepare(ko_gpu *g, cudaStream_t st)
+{
+    g->frozen = true;
+    if (!g->d_set && cudaMalloc(&g->d_set, sizeof(KoSet)) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    if (!g->d_acc && cudaMalloc(&g->d_acc, sizeof(KoAccum) * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    if (cudaMemcpyAsync(g->d_set, &g->h, sizeof(KoSet), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return KO_ERR_CUDA;
+    return KO_OK;
+}
+
+ko_status simple_scratch(ko_gpu *g, int64_t count)
+{
+    const size_t per = ko_simple_scratch_per_thread(g->h);
+    size_t slots = std::max<size_t>(128, std::min<size_t>(kSimpleScratchBudget / per, 152 * 8 * 128));
+    slots = std::min<size_t>(slots, (size_t)((count + 127) / 128) * 128);
+    slots = std::max<size_t>(slots, 128);
+    return grow(&g->scratch, &g->scratch_bytes, slots * per);
+}
+
+ko_status check_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return KO_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? KO_ERR_NOMEM : KO_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+ko_gpu *ko_create_gpu(int32_t n_sm, int32_t n_reg_sm, int32_t n_shm_sm, int32_t n_warp_sm,
+                      int32_t n_blk_sm)
+{
+    if (n_sm < 1 || n_sm > KO_MAX_SM || n_reg_sm < 1 || n_reg_sm > KO_MAX_CYCLES || n_shm_sm < 1 ||
+        n_shm_sm > KO_MAX_CYCLES || n_warp_sm < 1 || n_warp_sm > KO_MAX_CYCLES || n_blk_sm < 1 ||
+        n_blk_sm > KO_MAX_BLK_SM) {
+        fail(KO_ERR_ARG);
+        return nullptr;
+    }
+    ko_gpu *g = new (std::nothrow) ko_gpu();
+    if (!g) {
+        fail(KO_ERR_NOMEM);
+        return nullptr;
+    }
+    g->h.S = n_sm; g->h.R = n_reg_sm; g->h.Sh = n_shm_sm; g->h.W = n_warp_sm; g->h.Bk = n_blk_sm;
+    g->h.ccap = 32768; g->h.mcap = 32768;
+    g->h.cshift = 15; g->h.mshift = 15;
+    g->h.n = 0;
+    ok();
+    return g;
+}
+
+ko_status ko_set_capacity(ko_gpu *g, int64_t c_cap, int64_t m_cap)
+{
+    if (!g || c_cap < 1 || m_cap < 1 || c_cap > (int64_t(1) << 30) || m_cap > (int64_t(1) << 30))
+        return fail(KO_ERR_ARG);
+    if (g->frozen) return fail(KO_ERR_STATE);
+    g->h.ccap = c_cap; g->h.mcap = m_cap;
+    g->h.cshift = log2_exact(c_cap); g->h.mshift = log2_exact(m_cap);
+    return ok();
+}
+
+int32_t ko_add_kernel(ko_gpu *g, int32_t n_reg_i, int32_t n_shm_i, int32_t n_warp_i,
+                      int32_t n_tblk_i, int64_t c_i, int64_t m_i)
+{
+    if (!g || n_reg_i < 1 || n_shm_i < 0 || n_warp_i < 1 || n_tblk_i < 1 || n_tblk_i > (1 << 20) ||
+        c_i < 1 || m_i < 1 || c_i > KO_MAX_CYCLES || m_i > KO_MAX_CYCLES)
+        return fail(KO_ERR_ARG);
+    if (g->frozen) return fail(KO_ERR_STATE);
+    if (g->h.n >= KO_MAX_KERNELS) return fail(KO_ERR_ARG);
+    if (n_reg_i > g->h.R || n_shm_i > g->h.Sh || n_warp_i > g->h.W) return fail(KO_ERR_NOFIT);
+    KoKern &k = g->h.k[g->h.n];
+    k.r = n_reg_i; k.s = n_shm_i; k.w = n_warp_i; k.b = n_tblk_i;
+    k.c = (int32_t)c_i; k.m = (int32_t)m_i;
+    int64_t lb, ub;
+    g->h.n++;
+    if (!ko_bounds_host(g->h, &lb, &ub)) {
+        g->h.n--;
+        return fail(KO_ERR_OVERFLOW);
+    }
+    ok();
+    return g->h.n - 1;
+}
+
+int32_t ko_num_kernels(const ko_gpu *g)
+{
+    if (!g) return fail(KO_ERR_ARG);
+    ok();
+    return g->h.n;
+}
+
+ko_status ko_bounds(ko_gpu *g, int64_t *lb, int64_t *ub)
+{
+    if (!g || !lb || !ub) return fail(KO_ERR_ARG);
+    if (!ko_bounds_host(g->h, lb, ub)) return fail(KO_ERR_OVERFLOW);
+    return ok();
+}
+
+ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out)
+{
+    if (!g || (!order_out && g->h.n > 0)) return fail(KO_ERR_ARG);
+    if (g->h.n > 0) ko_heuristic_host(g->h, order_out);
+    return ok();
+}
+
+ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
+                         int64_t *makespan_out, void *stream)
+{
+    if (!g || n < 0 || (idx == nullptr) == (orders == nullptr) || (n > 0 && !makespan_out))
+        return fail(KO_ERR_ARG);
+    const int N = g->h.n;
+    if (idx && N > 20) return fail(KO_ERR_ARG);
+    if (n == 0) return ok();
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool out_dev = is_device_ptr(makespan_out);
+    if (N == 0) {
+        if (out_dev) {
+            if (cudaMemsetAsync(makespan_out, 0, sizeof(int64_t) * n, st) != cudaSuccess)
+                return fail(KO_ERR_CUDA);
+        } else {
+            std::memset(makespan_out, 0, sizeof(int64_t) * n);
+        }
+        return ok();
+    }
+    ko_status s = prepare(g, st);
+    if (s) return fail(s);
+    const void *in = idx ? (const void *)idx : (const void *)orders;
+    const size_t in_bytes = idx ? sizeof(uint64_t) * n : (size_t)n * N;
+    const bool in_dev = is_device_ptr(in);
+    size_t need = (in_dev ? 0 : (in_bytes + 255) / 256 * 256) + (out_dev ? 0 : sizeof(int64_t) * n);
+    if ((s = grow(&g->d_stage, &g->stage_cap, std::max<size_t>(need, 256)))) return fail(s);
+    char *stage = (char *)g->d_stage;
+    const void *d_in = in;
+    if (!in_dev) {
+        if (cudaMemcpyAsync(stage, in, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+        d_in = stage;
+        stage += (in_bytes + 255) / 256 * 256;
+    }
+    int64_t *d_out = out_dev ? makespan_out : (int64_t *)stage;
+    if (idx) {
+        // Lehmer-index lists go to the run-length simulator when it applies.
+        s = ko_fast_eval_idx(&g->fast, g->h, g->d_set, (const uint64_t *)d_in, n, d_out, st);
+        if (s < 0) return fail(s);
+        if (s == 1) {
+            if ((s = simple_scratch(g, n))) return fail(s);
+            if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, (const uint64_t *)d_in, 0,
+                                                 n, d_out, nullptr, g->scratch, g->scratch_bytes, st))))
+                return fail(s);
+        }
+    } else {
+        if ((s = simple_scratch(g, n))) return fail(s);
+        if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, (const int8_t *)d_in, nullptr, 0, n,
+                                             d_out, nullptr, g->scratch, g->scratch_bytes, st))))
+            return fail(s);
+    }
+    if (!out_dev) {
+        if (cudaMemcpyAsync(makespan_out, d_out, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+            return fail(KO_ERR_CUDA);
+    }
+    if (!in_dev || !out_dev) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
+    }
+    return ok();
+}
+
+}  // extern "C"
+
+namespace {
+
+// All N! makespans into d_out (device) and the accumulators, on `st`.
+ko_status exhaustive(ko_gpu *g, int64_t *d_out, KoAccum *d_acc, cudaStream_t st)
+{
+    const int64_t total = kFactorial[g->h.n];
+    ko_status s = check_cuda(ko_launch_accum_reset(d_acc, 1, st));
+    if (s) return s;
+    s = ko_fast_exhaustive(&g->fast, g->h, g->d_set, d_out, d_acc, st);
+    if (s == 1) {  // run-length simulator does not apply: simple simulator over all indices
+        if ((s = simple_scratch(g, total))) return s;
+        s = check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, nullptr, 0, total, d_out, d_acc,
+                                        g->scratch, g->scratch_bytes, st));
+    }
+    return s;
+}
+
+ko_status makespan_of(ko_gpu *g, const int32_t *order, int64_t *m, cudaStream_t st)
+{
+    const int N = g->h.n;
+    int8_t perm[KO_MAX_KERNELS];
+    for (int i = 0; i < N; i++) perm[i] = (int8_t)order[i];
+    ko_status s = grow(&g->d_stage, &g->stage_cap, 256 + sizeof(int64_t));
+    if (s) return s;
+    int8_t *d_perm = (int8_t *)g->d_stage;
+    int64_t *d_m = (int64_t *)((char *)g->d_stage + 256);
+    if (cudaMemcpyAsync(d_perm, perm, N, cudaMemcpyHostToDevice, st) != cudaSuccess) return KO_ERR_CUDA;
+    if ((s = simple_scratch(g, 1))) return s;
+    if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, d_perm, nullptr, 0, 1, d_m, nullptr,
+                                         g->scratch, g->scratch_bytes, st))))
+        return s;
+    if (cudaMemcpyAsync(m, d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return KO_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return KO_ERR_CUDA;
+    return KO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream)
+{
+    if (!g || !makespans_out || g->h.n < 1) return fail(KO_ERR_ARG);
+    if (g->h.n > KO_MAX_EXHAUSTIVE) return fail(KO_ERR_TOO_LARGE);
+    if (!is_device_ptr(makespans_out)) return fail(KO_ERR_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    g->h.ref_makespan = 0;
+    ko_status s = prepare(g, st);
+    if (s) return fail(s);
+    if ((s = exhaustive(g, makespans_out, g->d_acc, st))) return fail(s);
+    return ok();
+}
+
+ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t *hist,
+                        int32_t nbins, void *stream)
+{
+    if (!g || !out || (hist && (nbins < 1 || nbins > 32768)) || g->h.n < 1) return fail(KO_ERR_ARG);
+    const int N = g->h.n;
+    if (N > KO_MAX_EXHAUSTIVE) return fail(KO_ERR_TOO_LARGE);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> ord(N);
+    if (order) {
+        uint32_t seen = 0;
+        for (int i = 0; i < N; i++) {
+            if (order[i] < 0 || order[i] >= N || ((seen >> order[i]) & 1u)) return fail(KO_ERR_ARG);
+            seen |= 1u << order[i];
+            ord[i] = order[i];
+        }
+    } else {
+        ko_heuristic_host(g->h, ord.data());
+    }
+    g->h.ref_makespan = 0;
+    ko_status s = prepare(g, st);
+    if (s) return fail(s);
+    int64_t mh = 0;
+    if ((s = makespan_of(g, ord.data(), &mh, st))) return fail(s);
+    if (mh < 0) return fail(KO_ERR_STATE);
+    g->h.ref_makespan = mh;
+    if ((s = prepare(g, st))) return fail(s);
+    const int64_t total = kFactorial[N];
+    if ((s = grow((void **)&g->d_ms, &g->ms_cap, sizeof(int64_t) * total))) return fail(s);
+    if ((s = exhaustive(g, g->d_ms, g->d_acc, st))) return fail(s);
+    if (hist) {
+        if (g->hist_cap < nbins) {
+            cudaFree(g->d_hist);
+            g->d_hist = nullptr;
+            g->hist_cap = 0;
+            if (cudaMalloc(&g->d_hist, sizeof(unsigned long long) * nbins) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(KO_ERR_NOMEM);
+            }
+            g->hist_cap = nbins;
+        }
+        const bool hist_dev = is_device_ptr(hist);
+        unsigned long long *dh = hist_dev ? (unsigned long long *)hist : g->d_hist;
+        if (cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * nbins, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+        if ((s = check_cuda(ko_launch_histogram(g->d_ms, total, g->d_acc, dh, nbins, st))))
+            return fail(s);
+        if (!hist_dev && cudaMemcpyAsync(hist, dh, sizeof(unsigned long long) * nbins,
+                                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+    }
+    KoAccum acc;
+    if (cudaMemcpyAsync(&acc, g->d_acc, sizeof(KoAccum), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return fail(KO_ERR_CUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
+    if (acc.failed) return fail(KO_ERR_STATE);
+    out->min = (int64_t)acc.min;
+    out->max = (int64_t)acc.max;
+    out->makespan = mh;
+    out->n_total = (uint64_t)total;
+    out->n_better = acc.n_better;
+    out->n_equal = acc.n_equal;
+    out->n_worse = acc.n_worse;
+    out->percentile = 100.0 * (double)(acc.n_worse + acc.n_equal) / (double)total;
+    out->percentile_strict = 100.0 * (double)acc.n_worse / (double)total;
+    out->speedup_over_worst = (double)out->max / (double)mh;
+    out->deviation_from_optimal = (double)(mh - out->min) / (double)out->min;
+    return ok();
+}
+
+void ko_destroy_gpu(ko_gpu *g) { delete g; }
+
+const char *ko_status_str(ko_status s)
+{
+    switch (s) {
+    case KO_OK: return "KO_OK";
+    case KO_ERR_ARG: return "KO_ERR_ARG";
+    case KO_ERR_NOFIT: return "KO_ERR_NOFIT";
+    case KO_ERR_TOO_LARGE: return "KO_ERR_TOO_LARGE";
+    case KO_ERR_OVERFLOW: return "KO_ERR_OVERFLOW";
+    case KO_ERR_CUDA: return "KO_ERR_CUDA";
+    case KO_ERR_TIMEOUT: return "KO_ERR_TIMEOUT";
+    case KO_ERR_STATE: return "KO_ERR_STATE";
+    case KO_ERR_NOMEM: return "KO_ERR_NOMEM";
+    default: return "KO_ERR_UNKNOWN";
+    }
+}
+
+ko_status ko_last_error(void) { return t_last_error; }
+
+}  // extern "C"

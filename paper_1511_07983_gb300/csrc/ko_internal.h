@@ -1,0 +1,62 @@
+// Internal declarations shared by libko's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ko.h"
+
+// Per-block kernel descriptor (Table 1, last three rows): registers, shared
+// memory bytes, warps of one block, block count, compute and memory cycles of
+// one block running alone.
+struct KoKern {
+    int32_t r, s, w, b, c, m;
+};
+
+// Device-side description of one kernel set on one simulated GPU.
+struct KoSet {
+    int32_t n;                   // kernels in the set
+    int32_t S, R, Sh, W, Bk;     // N_SM and the four per-SM limits
+    int64_t ccap, mcap;          // compute / memory capacity (R_B = ccap / mcap)
+    int32_t cshift, mshift;      // log2(capacity) when a power of two, else -1
+    int64_t ref_makespan;        // makespan the exhaustive counts compare against
+    KoKern k[KO_MAX_KERNELS];
+};
+
+// Exhaustive accumulators of one set (device memory).
+struct KoAccum {
+    unsigned long long min, max;
+    unsigned long long n_better, n_equal, n_worse;
+    unsigned long long failed;   // simulations that could not finish
+};
+
+// ------------------------------------------------------------------ launchers
+// All launchers are asynchronous on `stream` and return the launch status.
+
+// Per-thread scratch bytes the simple simulator needs for one set.
+size_t ko_simple_scratch_per_thread(const KoSet &h);
+
+// Simple exact simulator, one thread per order.  Orders come from
+//   perms  (count x n int8 rows)            if perms != nullptr,
+//   idx    (count Lehmer indices)           else if idx != nullptr,
+//   first + j (contiguous Lehmer indices)   otherwise.
+// Writes makespans (if out != nullptr) and folds them into acc (if non-null).
+cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_t *perms,
+                             const uint64_t *idx, uint64_t first, int64_t count, int64_t *out,
+                             KoAccum *acc, void *scratch, size_t scratch_bytes,
+                             cudaStream_t stream);
+
+// Histogram of `count` makespans with bin = (M - min) * nbins / (max - min + 1),
+// min / max read from acc on the device; hist (device, nbins u64) is added to.
+cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum *acc,
+                                unsigned long long *hist, int32_t nbins, cudaStream_t stream);
+
+// Resets an accumulator to (min = max u64, max = 0, counts = 0).
+cudaError_t ko_launch_accum_reset(KoAccum *acc, int count, cudaStream_t stream);
+
+// Host-side Algorithm 1; returns the number of execution rounds.
+int ko_heuristic_host(const KoSet &h, int32_t *order_out);
+
+// Host-side bounds; returns false if the upper bound overflows 62 bits.
+bool ko_bounds_host(const KoSet &h, int64_t *lb, int64_t *ub);

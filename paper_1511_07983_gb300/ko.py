@@ -1,0 +1,247 @@
+"""ctypes binding of libko (include/ko.h): argument marshalling only.
+
+Every simulation step runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch tensors to pointers and raises on error codes.
+It loads ``_build/libko.so`` and fails loudly if the library was not built
+(``python -m paper_1511_07983_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import platform
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libko.so")
+
+KO_OK = 0
+STATUS = {0: "KO_OK", -1: "KO_ERR_ARG", -2: "KO_ERR_NOFIT", -3: "KO_ERR_TOO_LARGE",
+          -4: "KO_ERR_OVERFLOW", -5: "KO_ERR_CUDA", -6: "KO_ERR_TIMEOUT", -7: "KO_ERR_STATE",
+          -8: "KO_ERR_NOMEM"}
+
+
+class KoError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class ko_rank(ctypes.Structure):
+    _fields_ = [("min", ctypes.c_int64), ("max", ctypes.c_int64), ("makespan", ctypes.c_int64),
+                ("n_total", ctypes.c_uint64), ("n_better", ctypes.c_uint64),
+                ("n_equal", ctypes.c_uint64), ("n_worse", ctypes.c_uint64),
+                ("percentile", ctypes.c_double), ("percentile_strict", ctypes.c_double),
+                ("speedup_over_worst", ctypes.c_double), ("deviation_from_optimal", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+_SIGNATURES = {
+    "ko_create_gpu": (ctypes.c_void_p, [ctypes.c_int32] * 5),
+    "ko_set_capacity": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "ko_add_kernel": (ctypes.c_int32, [ctypes.c_void_p] + [ctypes.c_int32] * 4 + [ctypes.c_int64] * 2),
+    "ko_num_kernels": (ctypes.c_int32, [ctypes.c_void_p]),
+    "ko_bounds": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)]),
+    "ko_heuristic_order": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_eval_orders": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_rank_order": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ko_rank),
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "ko_eval_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_destroy_gpu": (None, [ctypes.c_void_p]),
+    "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "ko_last_error": (ctypes.c_int32, []),
+}
+
+
+def lib():
+    """Load libko.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libko.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str) -> int:
+    if code < 0:
+        raise KoError(code, what)
+    return code
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported buffer {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ----------------------------------------------------- C names, same arguments
+
+def ko_create_gpu(n_sm, n_reg_sm, n_shm_sm, n_warp_sm, n_blk_sm):
+    h = lib().ko_create_gpu(n_sm, n_reg_sm, n_shm_sm, n_warp_sm, n_blk_sm)
+    if not h:
+        raise KoError(lib().ko_last_error(), "ko_create_gpu")
+    return h
+
+
+def ko_set_capacity(g, c_cap, m_cap):
+    return _check(lib().ko_set_capacity(g, c_cap, m_cap), "ko_set_capacity")
+
+
+def ko_add_kernel(g, n_reg_i, n_shm_i, n_warp_i, n_tblk_i, c_i, m_i):
+    return _check(lib().ko_add_kernel(g, n_reg_i, n_shm_i, n_warp_i, n_tblk_i, c_i, m_i),
+                  "ko_add_kernel")
+
+
+def ko_num_kernels(g):
+    return _check(lib().ko_num_kernels(g), "ko_num_kernels")
+
+
+def ko_bounds(g):
+    lb, ub = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ko_bounds(g, ctypes.byref(lb), ctypes.byref(ub)), "ko_bounds")
+    return lb.value, ub.value
+
+
+def ko_heuristic_order(g):
+    n = ko_num_kernels(g)
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().ko_heuristic_order(g, _ptr(out)), "ko_heuristic_order")
+    return out[:n]
+
+
+def ko_eval_orders(g, idx=None, orders=None, out=None, stream=None):
+    """Makespans of orders given as Lehmer indices (uint64) or rows of kernel
+    ids (int8).  Inputs/outputs may be numpy (host) or torch CUDA tensors."""
+    src = idx if idx is not None else orders
+    count = int(src.shape[0]) if src is not None else 0
+    if out is None:
+        out = np.empty(count, dtype=np.int64)
+    _check(lib().ko_eval_orders(g, _ptr(idx), _ptr(orders), count, _ptr(out), _stream(stream)),
+           "ko_eval_orders")
+    return out
+
+
+def ko_rank_order(g, order=None, nbins=4096, hist=None, stream=None):
+    """Exhaustive scoring; returns (ko_rank dict, histogram or None)."""
+    r = ko_rank()
+    o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    if hist is None and nbins:
+        hist = np.zeros(nbins, dtype=np.uint64)
+    _check(lib().ko_rank_order(g, _ptr(o), ctypes.byref(r), _ptr(hist), int(nbins) if hist is not None else 0,
+                               _stream(stream)), "ko_rank_order")
+    return r.as_dict(), hist
+
+
+def ko_eval_all(g, out, stream=None):
+    return _check(lib().ko_eval_all(g, _ptr(out), _stream(stream)), "ko_eval_all")
+
+
+def ko_destroy_gpu(g):
+    lib().ko_destroy_gpu(g)
+
+
+def ko_status_str(code):
+    return lib().ko_status_str(code).decode()
+
+
+def ko_last_error():
+    return lib().ko_last_error()
+
+
+# ------------------------------------------------------------ convenience
+
+class Gpu:
+    """Owning wrapper of a ko_gpu handle."""
+
+    def __init__(self, n_sm, n_reg_sm, n_shm_sm, n_warp_sm, n_blk_sm, c_cap=None, m_cap=None):
+        self.h = ko_create_gpu(n_sm, n_reg_sm, n_shm_sm, n_warp_sm, n_blk_sm)
+        if c_cap is not None:
+            ko_set_capacity(self.h, c_cap, m_cap)
+
+    @classmethod
+    def from_set(cls, kset):
+        """Handle for a synth.KernelSet (gpu 7-tuple + int64 [N, 6] kernels)."""
+        g = cls(*kset.gpu[:5], c_cap=kset.gpu[5], m_cap=kset.gpu[6])
+        for row in np.asarray(kset.kernels).tolist():
+            g.add_kernel(*row)
+        return g
+
+    def add_kernel(self, n_reg, n_shm, n_warp, n_tblk, c, m):
+        return ko_add_kernel(self.h, n_reg, n_shm, n_warp, n_tblk, c, m)
+
+    @property
+    def n(self):
+        return ko_num_kernels(self.h)
+
+    def bounds(self):
+        return ko_bounds(self.h)
+
+    def heuristic_order(self):
+        return ko_heuristic_order(self.h)
+
+    def eval_orders(self, idx=None, orders=None, out=None, stream=None):
+        return ko_eval_orders(self.h, idx=idx, orders=orders, out=out, stream=stream)
+
+    def rank_order(self, order=None, nbins=4096, hist=None, stream=None):
+        return ko_rank_order(self.h, order=order, nbins=nbins, hist=hist, stream=stream)
+
+    def eval_all(self, out, stream=None):
+        return ko_eval_all(self.h, out, stream=stream)
+
+    def n_orders(self):
+        return math.factorial(self.n)
+
+    def close(self):
+        if self.h:
+            ko_destroy_gpu(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,105 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/*.h, validates arguments, and its host-side Algorithm 1 and
+bounds agree exactly with the oracle's."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_07983_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ko():
+    from paper_1511_07983_gb300 import build, ko as kmod
+    build.build()
+    kmod.lib()
+    return kmod
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(ko_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ko_create_gpu", "ko_add_kernel", "ko_eval_orders", "ko_rank_order",
+                     "ko_heuristic_order"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ko):
+    L = ko.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_argument_validation(ko):
+    with pytest.raises(ko.KoError) as e:
+        ko.ko_create_gpu(0, 65536, 49152, 64, 16)
+    assert e.value.code == -1
+    with pytest.raises(ko.KoError):
+        ko.ko_create_gpu(13, 65536, 49152, 64, 33)       # > 32 blocks per SM
+    g = ko.Gpu(2, 100, 100, 100, 4)
+    with pytest.raises(ko.KoError) as e:
+        g.add_kernel(101, 0, 1, 1, 1, 1)                 # block larger than an SM
+    assert e.value.code == -2
+    with pytest.raises(ko.KoError) as e:
+        g.add_kernel(10, 0, 1, 0, 1, 1)                  # zero blocks
+    assert e.value.code == -1
+    with pytest.raises(ko.KoError):
+        g.add_kernel(10, 0, 1, 1, 1, 1 << 25)             # cycles beyond 2^24
+    assert g.add_kernel(10, 0, 1, 1, 5, 5) == 0
+    assert g.n == 1
+    assert ko.ko_status_str(-3) == "KO_ERR_TOO_LARGE"
+    with pytest.raises(ko.KoError):
+        ko.ko_set_capacity(g.h, 0, 1)
+
+
+def _sets():
+    out = [synth.gen_set("single8"), synth.gen_set("single12")]
+    out += [synth.gen_set("sets10", i) for i in range(8)]
+    out += [synth.gen_set("batched", i) for i in range(40)]
+    out += [synth.gen_set("large", i) for i in range(20)]
+    out += [synth.random_set(s, 2 + s % 20, blk=(1, 300)) for s in range(60)]
+    return out
+
+
+def test_heuristic_matches_oracle(ko):
+    for s in _sets():
+        with ko.Gpu.from_set(s) as g:
+            assert g.heuristic_order().tolist() == oracle.heuristic(s.gpu, s.kernels)
+
+
+def test_heuristic_hand_traces(ko):
+    import json
+    cases = json.load(open(os.path.join(ROOT, "tests", "golden", "hand_traces.json")))["cases"]
+    for c in cases:
+        if "heuristic" not in c:
+            continue
+        g = ko.Gpu(*c["gpu"][:5], c_cap=c["gpu"][5], m_cap=c["gpu"][6])
+        for row in c["kernels"]:
+            g.add_kernel(*row)
+        assert g.heuristic_order().tolist() == c["heuristic"], c["name"]
+
+
+def test_bounds_match_oracle(ko):
+    for s in _sets():
+        with ko.Gpu.from_set(s) as g:
+            assert g.bounds() == oracle.bounds(s.gpu, s.kernels)
+
+
+def test_non_power_of_two_capacity_heuristic(ko):
+    s = synth.random_set(5, 9, blk=(1, 100), c_cap=3000, m_cap=7000)
+    with ko.Gpu.from_set(s) as g:
+        assert g.heuristic_order().tolist() == oracle.heuristic(s.gpu, s.kernels)
