@@ -128,9 +128,9 @@ ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out);
  * Exactly one of idx / orders is non-NULL:
  *   idx     n Lehmer indices in [0, N!)   (N <= 20), host or device;
  *   orders  n x N kernel ids, row-major, each row a permutation, host or device.
- * Rows are not checked for being permutations on the device; a row with an
- * id outside [0, N) yields makespan -1.  Asynchronous on `stream` when every
- * pointer is a device pointer; otherwise synchronises before returning. */
+ * A row that is not a permutation of 0..N-1 yields makespan -1.  Explicit
+ * rows are asynchronous on `stream` when both pointers are device pointers;
+ * index lists and host buffers synchronise `stream` before returning. */
 ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
                          int64_t *makespan_out, void *stream);
 
@@ -146,6 +146,32 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
 /* Makespans of all N! orders in Lehmer-index order into makespans_out[N!]
  * (device memory), N <= 12.  Asynchronous on `stream`. */
 ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
+
+/* Tuning knobs of the device simulators (set by the tuner; per handle).
+ *   KO_OPT_LANES        lanes that share one simulation in the run-length
+ *                       simulator: 16 or 32 (default 32)
+ *   KO_OPT_LEVELS       prefix-sharing depth: exhaustive work items fix the
+ *                       first N-1-levels kernels and walk the rest depth
+ *                       first, saving `levels` states; 0..6 (default 4)
+ *   KO_OPT_SIMPLE_ONLY  1 = use only the simple one-thread-per-order
+ *                       simulator, 0 = run-length simulator where it applies
+ *   KO_OPT_RUN_LIMIT    most runs of distinct SM states one simulation may
+ *                       hold before its work item moves to the simple
+ *                       simulator, 1..32 (default 32; small values exercise
+ *                       that hand-over)
+ * Results never depend on these knobs.  KO_ERR_ARG for an unknown key or
+ * value. */
+#define KO_OPT_LANES 1
+#define KO_OPT_LEVELS 2
+#define KO_OPT_SIMPLE_ONLY 3
+#define KO_OPT_RUN_LIMIT 4
+ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
+
+/* Work items the last exhaustive or index-list call moved from the
+ * run-length simulator to the simple one (a simulation needed more runs of
+ * distinct SM states than lanes, or more than 8 resident groups in a run);
+ * -1 for a NULL handle.  Informational: results are exact either way. */
+int64_t ko_last_fallback_items(const ko_gpu *g);
 
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);

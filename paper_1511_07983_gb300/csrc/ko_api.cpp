@@ -278,6 +278,7 @@ ko_status exhaustive(ko_gpu *g, int64_t *d_out, KoAccum *d_acc, cudaStream_t st)
     if (s) return s;
     s = ko_fast_exhaustive(&g->fast, g->h, g->d_set, d_out, d_acc, st);
     if (s == 1) {  // run-length simulator does not apply: simple simulator over all indices
+        if ((s = check_cuda(ko_launch_accum_reset(d_acc, 1, st)))) return s;
         if ((s = simple_scratch(g, total))) return s;
         s = check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, nullptr, 0, total, d_out, d_acc,
                                         g->scratch, g->scratch_bytes, st));
@@ -390,6 +391,34 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
     out->deviation_from_optimal = (double)(mh - out->min) / (double)out->min;
     return ok();
 }
+
+ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
+{
+    if (!g) return fail(KO_ERR_ARG);
+    switch (key) {
+    case KO_OPT_LANES:
+        if (value != 16 && value != 32) return fail(KO_ERR_ARG);
+        g->fast.lanes = (int)value;
+        break;
+    case KO_OPT_LEVELS:
+        if (value < 0 || value > 6) return fail(KO_ERR_ARG);
+        g->fast.levels = (int)value;
+        break;
+    case KO_OPT_SIMPLE_ONLY:
+        if (value != 0 && value != 1) return fail(KO_ERR_ARG);
+        g->fast.disabled = value == 1;
+        break;
+    case KO_OPT_RUN_LIMIT:
+        if (value < 1 || value > 32) return fail(KO_ERR_ARG);
+        g->fast.run_limit = (int)value;
+        break;
+    default:
+        return fail(KO_ERR_ARG);
+    }
+    return ok();
+}
+
+int64_t ko_last_fallback_items(const ko_gpu *g) { return g ? (int64_t)g->fast.last_overflow : -1; }
 
 void ko_destroy_gpu(ko_gpu *g) { delete g; }
 

@@ -1,16 +1,674 @@
-// Run-length, prefix-sharing simulator: not built yet, always defers.
+// Run-length, prefix-sharing simulator of the block-dispatch model.
+//
+// Same model as the simple simulator (Sec. 2 dispatch rule; durations fixed at
+// burst end from the SM's SumC / SumM), organised for throughput:
+//
+// * Runs.  SMs with identical state (usage, SumC, SumM and resident groups
+//   with identical end times) form a run of consecutive SM indices.  One lane
+//   of a LANES-wide segment (16 or 32 lanes of a warp) holds one run in
+//   registers.  Runs are split only where SMs of a run receive different
+//   numbers of blocks; the number of runs stays small because the round-robin
+//   dispatch treats consecutive SMs alike.
+// * Bulk round-robin.  Placing the head kernel is a water-fill: each SM of
+//   run j takes at most cap_j more blocks (min over the four limits), sweeps go
+//   cyclically from the round-robin pointer p and give one block to every SM
+//   with capacity left, so after the placement every SM holds min(cap, L-1)
+//   blocks plus one for the first `rem` SMs (cyclic from p) with cap >= L.
+//   This reproduces block-by-block first-fit exactly.
+// * Groups.  Blocks of one kernel started in one burst on one SM end together
+//   and are kept as one group (kernel, count per SM, end).
+// * Time.  Ends are kept as 32-bit values modulo 2^32 next to a 64-bit clock;
+//   every live end lies within (t, t + max duration] and the host only uses
+//   this path when every duration is below 2^31, so comparisons are exact.
+// * Prefix sharing.  The lexicographic order of Lehmer indices is a DFS over
+//   kernel choices; the state after placing a prefix is saved in shared memory
+//   and restored for each sibling, so each order only pays for the kernels in
+//   which it differs from its predecessor (about e kernels per order).
+//   The state at a DFS node is "prefix placed, current burst still open":
+//   the next kernel continues the same burst.
+// * Overflow.  A segment that would need more runs than lanes, or more than
+//   kG groups in one run, abandons its work item and records it; the host
+//   re-runs recorded items with the simple simulator.
 #include "ko_fast.h"
 
-ko_status ko_fast_exhaustive(KoFastState *, const KoSet &, const KoSet *, int64_t *, KoAccum *,
-                             cudaStream_t)
+namespace {
+
+constexpr int kG = 8;                       // group slots per run
+constexpr uint32_t kPend = 1u << 15;        // group started in the open burst
+constexpr uint32_t kValid = 1u << 16;       // slot holds a group
+// group word: kernel id (bits 0-4) | blocks per SM (bits 8-13) | kPend | kValid
+
+constexpr int kMaxLevels = 6;               // saved DFS levels per segment
+constexpr int kStateWords = 8 + 2 * kG;     // per-lane registers saved per level
+constexpr int kThreads = 128;
+
+__constant__ unsigned long long c_fact[21] = {
+    1ull, 1ull, 2ull, 6ull, 24ull, 120ull, 720ull, 5040ull, 40320ull, 362880ull, 3628800ull,
+    39916800ull, 479001600ull, 6227020800ull, 87178291200ull, 1307674368000ull,
+    20922789888000ull, 355687428096000ull, 6402373705728000ull, 121645100408832000ull,
+    2432902008176640000ull};
+
+struct SetConst {
+    int n, S, R, Sh, W, Bk;
+    long long ccap, mcap;
+    int cshift, mshift;
+    long long ref;
+    int total_blocks;
+    int r[KO_MAX_KERNELS], s[KO_MAX_KERNELS], w[KO_MAX_KERNELS], b[KO_MAX_KERNELS];
+    int c[KO_MAX_KERNELS], m[KO_MAX_KERNELS];
+};
+
+struct FastArgs {
+    const KoSet *set;
+    int mode;                   // 0 = exhaustive over prefix items, 1 = explicit index list
+    int d0;                     // prefix depth of a work item (mode 0)
+    long long n_items;
+    const uint64_t *idx;        // mode 1
+    int64_t *out;               // makespans (nullable in mode 0)
+    KoAccum *acc;               // nullable
+    unsigned long long *counter;     // work counter
+    unsigned long long *ov_count;    // abandoned items
+    unsigned long long *ov_list;
+    unsigned long long ov_cap;
+    int levels;                 // saved levels per segment
+    int run_limit;              // runs a segment may hold (<= LANES)
+};
+
+template <int LANES>
+struct Seg {
+    unsigned mask;   // lanes of this segment
+    int lane;        // lane within segment
+};
+
+template <int LANES>
+__device__ __forceinline__ unsigned seg_ballot(const Seg<LANES> &sg, bool pred)
 {
-    return 1;
+    unsigned b = __ballot_sync(sg.mask, pred);
+    if (LANES == 32) return b;
+    return (b & sg.mask) >> (__ffs(sg.mask) - 1);
 }
 
-ko_status ko_fast_eval_idx(KoFastState *, const KoSet &, const KoSet *, const uint64_t *, int64_t,
-                           int64_t *, cudaStream_t)
+// Per-lane run state, held in registers (all array indices are compile-time).
+struct Run {
+    int beg, cnt, ur, us, uw, ub, sc, sm;
+    uint32_t gk[kG];
+    uint32_t ge[kG];
+};
+
+template <int LANES>
+struct Sim {
+    Seg<LANES> sg;
+    Run run;
+    long long t;     // clock (segment-uniform)
+    int p;           // round-robin pointer
+    int nruns;
+    int run_limit;
+    int fail;
+
+    __device__ __forceinline__ int shfl(int v, int src) const
+    {
+        return __shfl_sync(sg.mask, v, src, LANES);
+    }
+    __device__ __forceinline__ uint32_t shflu(uint32_t v, int src) const
+    {
+        return __shfl_sync(sg.mask, v, src, LANES);
+    }
+
+    __device__ void init(const SetConst &K)
+    {
+        run.beg = 0;
+        run.cnt = sg.lane == 0 ? K.S : 0;
+        run.ur = run.us = run.uw = run.ub = run.sc = run.sm = 0;
+#pragma unroll
+        for (int g = 0; g < kG; g++) { run.gk[g] = 0; run.ge[g] = 0; }
+        t = 0;
+        p = 0;
+        nruns = 1;
+        fail = 0;
+    }
+
+    // Split run j at offset x (0 < x < cnt_j): lane j keeps the first x SMs,
+    // lane j+1 takes the rest; later lanes move up one.  `extra` registers move
+    // with the lanes.
+    __device__ void split(int j, int x, int &extra0, int &extra1)
+    {
+        if (nruns >= run_limit) { fail = 1; return; }
+        const bool up = sg.lane > j;
+#define KO_SHIFT(v) { auto _u = __shfl_up_sync(sg.mask, v, 1, LANES); if (up) v = _u; }
+        KO_SHIFT(run.beg) KO_SHIFT(run.cnt) KO_SHIFT(run.ur) KO_SHIFT(run.us) KO_SHIFT(run.uw)
+        KO_SHIFT(run.ub) KO_SHIFT(run.sc) KO_SHIFT(run.sm) KO_SHIFT(extra0) KO_SHIFT(extra1)
+#pragma unroll
+        for (int g = 0; g < kG; g++) { KO_SHIFT(run.gk[g]) KO_SHIFT(run.ge[g]) }
+#undef KO_SHIFT
+        if (sg.lane == j) run.cnt = x;
+        if (sg.lane == j + 1) { run.beg += x; run.cnt -= x; }
+        nruns++;
+    }
+
+    // Add `give` blocks per SM of kernel kid to this lane's run as a new
+    // pending group.
+    __device__ void add_blocks(const SetConst &K, int kid, int give)
+    {
+        bool need = give > 0 && run.cnt > 0;
+        if (need) {
+            run.ur += give * K.r[kid];
+            run.us += give * K.s[kid];
+            run.uw += give * K.w[kid];
+            run.ub += give;
+            run.sc += give * K.c[kid];
+            run.sm += give * K.m[kid];
+        }
+        bool placed = !need;
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            if (!placed && run.gk[g] == 0) {
+                run.gk[g] = kValid | kPend | ((uint32_t)give << 8) | (uint32_t)kid;
+                placed = true;
+            }
+        }
+        if (__any_sync(sg.mask, !placed)) fail = 1;
+    }
+
+    // One dispatch burst for the head kernel `kid` with `left` blocks queued.
+    __device__ void burst(const SetConst &K, int kid, int &left)
+    {
+        const int r = K.r[kid], s = K.s[kid], w = K.w[kid];
+        int cap = 0;
+        if (run.cnt > 0) {
+            cap = K.Bk - run.ub;
+            cap = min(cap, (K.R - run.ur) / r);
+            cap = min(cap, (K.W - run.uw) / w);
+            if (s > 0) cap = min(cap, (K.Sh - run.us) / s);
+            cap = max(cap, 0);
+        }
+        const int total = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * cap));
+        if (total == 0) return;
+        const int maxcap = (int)__reduce_max_sync(sg.mask, (unsigned)cap);
+        if (total <= left) {
+            // every SM takes its full capacity; the last block lands on the SM
+            // with cap == maxcap that comes last cyclically from p
+            int pos = -1;
+            if (run.cnt > 0 && cap == maxcap) {
+                const int pm1 = p == 0 ? K.S - 1 : p - 1;
+                if (pm1 >= run.beg && pm1 < run.beg + run.cnt) pos = K.S - 1;
+                else { pos = run.beg + run.cnt - 1 - p; if (pos < 0) pos += K.S; }
+            }
+            const int maxpos = __reduce_max_sync(sg.mask, pos);
+            p += maxpos + 1;
+            if (p >= K.S) p -= K.S;
+            left -= total;
+            add_blocks(K, kid, cap);
+            return;
+        }
+        // partial placement: smallest sweep count L with F(L) >= left
+        int lo = 1, hi = maxcap;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int f = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * min(cap, mid)));
+            if (f >= left) hi = mid; else lo = mid + 1;
+        }
+        const int L = lo;
+        const int full = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * min(cap, L - 1)));
+        const int rem = left - full;  // 1 .. number of SMs with cap >= L
+        // the run holding p is cut at p when its SMs are eligible, so that the
+        // cyclic order from p is a rotation of whole runs
+        int jp = __ffs(seg_ballot(sg, run.cnt > 0 && run.beg <= p && p < run.beg + run.cnt)) - 1;
+        {
+            const int beg_jp = shfl(run.beg, jp), cap_jp = shfl(cap, jp);
+            if (beg_jp < p && cap_jp >= L) {
+                int dummy = 0;
+                split(jp, p - beg_jp, cap, dummy);
+                if (fail) return;
+                jp++;
+            }
+        }
+        const int e = (run.cnt > 0 && cap >= L) ? run.cnt : 0;
+        int incl = e;
+#pragma unroll
+        for (int o = 1; o < LANES; o <<= 1) {
+            const int v = __shfl_up_sync(sg.mask, incl, o, LANES);
+            if (sg.lane >= o) incl += v;
+        }
+        const int excl = incl - e;
+        const int E = shfl(incl, LANES - 1);
+        const int excl_jp = shfl(excl, jp);
+        const int rot = sg.lane >= jp ? excl - excl_jp : E - excl_jp + excl;
+        const int star = __ffs(seg_ballot(sg, e > 0 && rot < rem && rem <= rot + e)) - 1;
+        const int x = rem - shfl(rot, star);
+        const int cnt_star = shfl(run.cnt, star);
+        const int beg_star = shfl(run.beg, star);
+        // rotated position of each lane relative to jp
+        const int rl = sg.lane >= jp ? sg.lane - jp : sg.lane - jp + nruns;
+        const int rs = star >= jp ? star - jp : star - jp + nruns;
+        int plus = (e > 0 && rl < rs) ? 1 : 0;
+        if (sg.lane == star) plus = 1;
+        if (x < cnt_star) {
+            split(star, x, cap, plus);
+            if (fail) return;
+            if (sg.lane == star + 1) plus = 0;
+        }
+        p = beg_star + x;
+        if (p >= K.S) p -= K.S;
+        left = 0;
+        add_blocks(K, kid, min(cap, L - 1) + plus);
+    }
+
+    __device__ __forceinline__ uint32_t duration(const SetConst &K, int kid) const
+    {
+        const unsigned long long c = (unsigned long long)K.c[kid];
+        const unsigned long long m = (unsigned long long)K.m[kid];
+        const unsigned long long sc = (unsigned long long)max((long long)run.sc, K.ccap);
+        const unsigned long long sm = (unsigned long long)max((long long)run.sm, K.mcap);
+        unsigned long long dc, dm;
+        if (K.cshift >= 0) dc = (c * sc + (unsigned long long)K.ccap - 1) >> K.cshift;
+        else dc = (c * sc + (unsigned long long)K.ccap - 1) / (unsigned long long)K.ccap;
+        if (K.mshift >= 0) dm = (m * sm + (unsigned long long)K.mcap - 1) >> K.mshift;
+        else dm = (m * sm + (unsigned long long)K.mcap - 1) / (unsigned long long)K.mcap;
+        return (uint32_t)(dc > dm ? dc : dm);
+    }
+
+    // Fix the durations of the groups started in the open burst.
+    __device__ void close_burst(const SetConst &K)
+    {
+        const uint32_t t32 = (uint32_t)t;
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            if (__any_sync(sg.mask, (run.gk[g] & kPend) != 0)) {
+                if (run.gk[g] & kPend) {
+                    run.ge[g] = t32 + duration(K, run.gk[g] & 31u);
+                    run.gk[g] &= ~kPend;
+                }
+            }
+        }
+    }
+
+    // Jump to the earliest end and release every group ending then.
+    __device__ void advance(const SetConst &K)
+    {
+        const uint32_t t32 = (uint32_t)t;
+        uint32_t dmin = 0xffffffffu;
+#pragma unroll
+        for (int g = 0; g < kG; g++)
+            if (run.gk[g]) dmin = min(dmin, run.ge[g] - t32);
+        dmin = __reduce_min_sync(sg.mask, dmin);
+        if (dmin == 0xffffffffu) { fail = 1; return; }
+        t += dmin;
+        const uint32_t now = t32 + dmin;
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            const bool rel = run.gk[g] != 0 && run.ge[g] == now;
+            if (__any_sync(sg.mask, rel)) {
+                if (rel) {
+                    const int kid = run.gk[g] & 31u;
+                    const int q = (run.gk[g] >> 8) & 63u;
+                    run.ur -= q * K.r[kid]; run.us -= q * K.s[kid]; run.uw -= q * K.w[kid];
+                    run.ub -= q; run.sc -= q * K.c[kid]; run.sm -= q * K.m[kid];
+                    run.gk[g] = 0;
+                }
+            }
+        }
+    }
+
+    // Queue all blocks of kernel kid behind the current queue and simulate
+    // until the last of them is placed (the burst that places it stays open).
+    __device__ void place_kernel(const SetConst &K, int kid)
+    {
+        int left = K.b[kid];
+        for (int it = 0; !fail; it++) {
+            burst(K, kid, left);
+            if (left == 0 || fail) break;
+            close_burst(K);
+            advance(K);
+            if (it > K.total_blocks + 64) { fail = 1; break; }  // each event frees >= 1 block
+        }
+    }
+
+    // Close the final burst; the makespan is the latest end.
+    __device__ long long finish(const SetConst &K)
+    {
+        close_burst(K);
+        const uint32_t t32 = (uint32_t)t;
+        uint32_t dmax = 0;
+#pragma unroll
+        for (int g = 0; g < kG; g++)
+            if (run.gk[g]) dmax = max(dmax, run.ge[g] - t32);
+        dmax = __reduce_max_sync(sg.mask, dmax);
+        return t + (long long)dmax;
+    }
+
+    __device__ void save(int *slot) const
+    {
+        int *q = slot + sg.lane;
+        q[0 * LANES] = run.beg; q[1 * LANES] = run.cnt; q[2 * LANES] = run.ur;
+        q[3 * LANES] = run.us; q[4 * LANES] = run.uw; q[5 * LANES] = run.ub;
+        q[6 * LANES] = run.sc; q[7 * LANES] = run.sm;
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            q[(8 + g) * LANES] = (int)run.gk[g];
+            q[(8 + kG + g) * LANES] = (int)run.ge[g];
+        }
+        if (sg.lane == 0) {
+            int *u = slot + kStateWords * LANES;
+            u[0] = (int)(t & 0xffffffffll); u[1] = (int)(t >> 32); u[2] = p; u[3] = nruns;
+        }
+        __syncwarp(sg.mask);
+    }
+
+    __device__ void restore(const int *slot)
+    {
+        const int *q = slot + sg.lane;
+        run.beg = q[0 * LANES]; run.cnt = q[1 * LANES]; run.ur = q[2 * LANES];
+        run.us = q[3 * LANES]; run.uw = q[4 * LANES]; run.ub = q[5 * LANES];
+        run.sc = q[6 * LANES]; run.sm = q[7 * LANES];
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            run.gk[g] = (uint32_t)q[(8 + g) * LANES];
+            run.ge[g] = (uint32_t)q[(8 + kG + g) * LANES];
+        }
+        const int *u = slot + kStateWords * LANES;
+        t = (long long)(uint32_t)u[0] | ((long long)u[1] << 32);
+        p = u[2];
+        nruns = u[3];
+        fail = 0;
+    }
+};
+
+__device__ void load_const(SetConst &K, const KoSet *d)
 {
-    return 1;
+    if (threadIdx.x == 0) {
+        K.n = d->n; K.S = d->S; K.R = d->R; K.Sh = d->Sh; K.W = d->W; K.Bk = d->Bk;
+        K.ccap = d->ccap; K.mcap = d->mcap; K.cshift = d->cshift; K.mshift = d->mshift;
+        K.ref = d->ref_makespan;
+        int tb = 0;
+        for (int i = 0; i < d->n; i++) tb += d->k[i].b;
+        K.total_blocks = tb;
+    }
+    for (int i = threadIdx.x; i < KO_MAX_KERNELS; i += blockDim.x) {
+        K.r[i] = d->k[i].r; K.s[i] = d->k[i].s; K.w[i] = d->k[i].w;
+        K.b[i] = d->k[i].b; K.c[i] = d->k[i].c; K.m[i] = d->k[i].m;
+    }
+}
+
+// first `depth` kernels of the lexicographic permutation with Lehmer index k
+__device__ void lehmer_prefix(int n, unsigned long long k, int depth, int8_t *perm, uint32_t &used)
+{
+    used = 0;
+    for (int j = 0; j < depth; j++) {
+        const unsigned long long f = c_fact[n - 1 - j];
+        const uint32_t dgt = (uint32_t)(k / f);
+        k -= (unsigned long long)dgt * f;
+        uint32_t u = ~used & ((1u << n) - 1u);
+        for (uint32_t q = 0; q < dgt; q++) u &= u - 1u;
+        const int v = __ffs(u) - 1;
+        perm[j] = (int8_t)v;
+        used |= 1u << v;
+    }
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(kThreads)
+fast_kernel(FastArgs a)
+{
+    __shared__ SetConst K;
+    extern __shared__ int stack_mem[];
+    load_const(K, a.set);
+    __syncthreads();
+
+    constexpr int kSegs = kThreads / LANES;
+    Sim<LANES> sim;
+    const int seg = threadIdx.x / LANES;
+    sim.sg.lane = threadIdx.x % LANES;
+    sim.run_limit = a.run_limit < LANES ? a.run_limit : LANES;
+    sim.sg.mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+    const int level_words = kStateWords * LANES + 4;
+    int *stack = stack_mem + seg * a.levels * level_words;
+    (void)kSegs;
+
+    const int n = K.n;
+    const long long ref = K.ref;
+    unsigned long long smin = ~0ull, smax = 0, sb = 0, se = 0, sw = 0;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (sim.sg.lane == 0) item = atomicAdd(a.counter, 1ull);
+        item = __shfl_sync(sim.sg.mask, item, 0, LANES);
+        if (item >= (unsigned long long)a.n_items) break;
+
+        int8_t perm[KO_MAX_KERNELS];
+        uint32_t used;
+        int d0;
+        unsigned long long base;
+        if (a.mode == 1) {
+            d0 = n;
+            base = item;
+            const unsigned long long k = a.idx[item];
+            if (k >= c_fact[n]) {  // not a Lehmer index of this set
+                if (sim.sg.lane == 0 && a.out) a.out[base] = -1;
+                continue;
+            }
+            lehmer_prefix(n, k, n, perm, used);
+        } else {
+            d0 = a.d0;
+            base = item * c_fact[n - d0];
+            lehmer_prefix(n, base, d0, perm, used);
+        }
+        sim.init(K);
+        for (int j = 0; j < d0 && !sim.fail; j++) sim.place_kernel(K, perm[j]);
+
+        unsigned long long imin = ~0ull, imax = 0, ib = 0, ie = 0, iw = 0;
+        unsigned long long leaf = 0;
+        if (d0 == n) {
+            if (!sim.fail) {
+                const long long ms = sim.finish(K);
+                if (sim.sg.lane == 0) {
+                    if (a.out) a.out[base] = ms;
+                    imin = imax = (unsigned long long)ms;
+                    ib = ms < ref; ie = ms == ref; iw = ms > ref;
+                }
+            }
+        } else {
+            // lexicographic DFS below the prefix
+            int depth = d0;
+            int next[KO_MAX_KERNELS + 1];
+            next[depth] = 0;
+            bool first_child = true;
+            if (!sim.fail && n - depth >= 2) sim.save(stack + (depth - d0) * level_words);
+            while (!sim.fail) {
+                // next unused kernel id >= next[depth]
+                const uint32_t avail = ~used & ((1u << n) - 1u) & ~((1u << next[depth]) - 1u);
+                if (avail == 0) {
+                    if (depth == d0) break;
+                    depth--;
+                    const int prev = perm[depth];
+                    used &= ~(1u << prev);
+                    next[depth] = prev + 1;
+                    first_child = false;
+                    continue;
+                }
+                const int cand = __ffs(avail) - 1;
+                if (!first_child) sim.restore(stack + (depth - d0) * level_words);
+                perm[depth] = (int8_t)cand;
+                used |= 1u << cand;
+                sim.place_kernel(K, cand);
+                if (sim.fail) break;
+                if (depth + 1 == n) {
+                    const long long ms = sim.finish(K);
+                    if (sim.sg.lane == 0) {
+                        if (a.out) a.out[base + leaf] = ms;
+                        const unsigned long long u = (unsigned long long)ms;
+                        imin = u < imin ? u : imin;
+                        imax = u > imax ? u : imax;
+                        ib += ms < ref; ie += ms == ref; iw += ms > ref;
+                    }
+                    leaf++;
+                    used &= ~(1u << cand);
+                    next[depth] = cand + 1;
+                    first_child = false;
+                    continue;
+                }
+                depth++;
+                next[depth] = 0;
+                first_child = true;
+                if (n - depth >= 2) sim.save(stack + (depth - d0) * level_words);
+            }
+        }
+        if (sim.fail) {
+            if (sim.sg.lane == 0) {
+                const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
+                if (slot < a.ov_cap) a.ov_list[slot] = item;
+            }
+        } else {
+            smin = imin < smin ? imin : smin;
+            smax = imax > smax ? imax : smax;
+            sb += ib; se += ie; sw += iw;
+        }
+    }
+    if (a.acc && sim.sg.lane == 0) {
+        if (smin != ~0ull) atomicMin(&a.acc->min, smin);
+        if (smax) atomicMax(&a.acc->max, smax);
+        if (sb) atomicAdd(&a.acc->n_better, sb);
+        if (se) atomicAdd(&a.acc->n_equal, se);
+        if (sw) atomicAdd(&a.acc->n_worse, sw);
+    }
+}
+
+// Device buffer layout inside KoFastState::buf.
+struct FastBuf {
+    unsigned long long counter, ov_count, pad[6];
+    unsigned long long ov_list[1];
+};
+
+constexpr unsigned long long kOvCap = 1 << 20;
+
+unsigned long long c_fact_host(int n)
+{
+    unsigned long long f = 1;
+    for (int i = 2; i <= n; i++) f *= (unsigned long long)i;
+    return f;
+}
+
+bool applicable(const KoSet &h)
+{
+    if (h.n < 1) return false;
+    int64_t cmax = 0, mmax = 0;
+    for (int i = 0; i < h.n; i++) {
+        cmax = h.k[i].c > cmax ? h.k[i].c : cmax;
+        mmax = h.k[i].m > mmax ? h.k[i].m : mmax;
+    }
+    // every duration must stay below 2^31 for the modular end times
+    const __int128 sc = (__int128)h.Bk * cmax, sm = (__int128)h.Bk * mmax;
+    const __int128 dc = ((__int128)cmax * (sc > h.ccap ? sc : h.ccap) + h.ccap - 1) / h.ccap;
+    const __int128 dm = ((__int128)mmax * (sm > h.mcap ? sm : h.mcap) + h.mcap - 1) / h.mcap;
+    return dc < ((__int128)1 << 31) && dm < ((__int128)1 << 31);
+}
+
+ko_status ensure_buf(KoFastState *fs)
+{
+    const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * kOvCap;
+    if (fs->cap >= need) return KO_OK;
+    cudaFree(fs->buf);
+    fs->buf = nullptr;
+    fs->cap = 0;
+    if (cudaMalloc(&fs->buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    fs->cap = need;
+    return KO_OK;
+}
+
+template <int LANES>
+cudaError_t launch(const FastArgs &a, cudaStream_t st)
+{
+    const int level_words = kStateWords * LANES + 4;
+    const size_t smem = sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
+    cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const long long segs_needed = a.n_items;
+    const long long blocks_needed = (segs_needed + kThreads / LANES - 1) / (kThreads / LANES);
+    if (blocks > blocks_needed) blocks = blocks_needed;
+    if (blocks < 1) blocks = 1;
+    fast_kernel<LANES><<<(unsigned)blocks, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace {
+
+// Launch the fast kernel, then re-run every abandoned item with the simple
+// simulator (on the device, from the recorded list).  span = orders per item.
+ko_status run_fast(KoFastState *fs, const KoSet &h, const KoSet *d_set, FastArgs a,
+                   unsigned long long span, KoAccum *acc, cudaStream_t st)
+{
+    ko_status s = ensure_buf(fs);
+    if (s) return s;
+    FastBuf *fb = (FastBuf *)fs->buf;
+    if (cudaMemsetAsync(fb, 0, sizeof(FastBuf), st) != cudaSuccess) return KO_ERR_CUDA;
+    a.counter = &fb->counter;
+    a.ov_count = &fb->ov_count;
+    a.ov_list = fb->ov_list;
+    a.ov_cap = kOvCap;
+    a.run_limit = fs->run_limit;
+    cudaError_t e = fs->lanes == 16 ? launch<16>(a, st) : launch<32>(a, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_CUDA;
+    }
+    unsigned long long cnt = 0;
+    if (cudaMemcpyAsync(&cnt, &fb->ov_count, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return KO_ERR_CUDA;
+    fs->last_overflow = cnt;
+    if (cnt == 0) return KO_OK;
+    if (cnt > kOvCap) return 1;  // too many abandoned items: caller redoes everything
+    s = ko_simple_items(h, d_set, a.mode == 1 ? a.idx : nullptr, fb->ov_list, (long long)cnt, span,
+                        a.out, acc, st);
+    return s;
+}
+
+}  // namespace
+
+ko_status ko_fast_exhaustive(KoFastState *fs, const KoSet &h, const KoSet *d_set, int64_t *d_out,
+                             KoAccum *d_acc, cudaStream_t st)
+{
+    if (fs->disabled || !applicable(h) || h.n > KO_MAX_EXHAUSTIVE) return 1;
+    FastArgs a{};
+    a.set = d_set;
+    a.mode = 0;
+    int levels = fs->levels;
+    if (levels > kMaxLevels) levels = kMaxLevels;
+    int d0 = h.n - 1 - levels;
+    if (d0 < 0) d0 = 0;
+    a.d0 = d0;
+    a.levels = h.n - 1 - d0 > 0 ? h.n - 1 - d0 : 1;
+    a.n_items = (long long)(c_fact_host(h.n) / c_fact_host(h.n - d0));
+    a.out = d_out;
+    a.acc = d_acc;
+    return run_fast(fs, h, d_set, a, c_fact_host(h.n - d0), d_acc, st);
+}
+
+ko_status ko_fast_eval_idx(KoFastState *fs, const KoSet &h, const KoSet *d_set,
+                           const uint64_t *d_idx, int64_t count, int64_t *d_out, cudaStream_t st)
+{
+    if (fs->disabled || !applicable(h) || h.n > 20) return 1;
+    FastArgs a{};
+    a.set = d_set;
+    a.mode = 1;
+    a.d0 = h.n;
+    a.levels = 1;
+    a.n_items = count;
+    a.idx = d_idx;
+    a.out = d_out;
+    a.acc = nullptr;
+    return run_fast(fs, h, d_set, a, 1, nullptr, st);
 }
 
 void ko_fast_release(KoFastState *fs)

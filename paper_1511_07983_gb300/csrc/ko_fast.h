@@ -5,8 +5,13 @@
 
 // Device buffers the run-length simulator keeps between calls.
 struct KoFastState {
-    void *buf = nullptr;   // work items, overflow list, counters
+    void *buf = nullptr;   // work counter, abandoned-item list
     size_t cap = 0;
+    unsigned long long last_overflow = 0;  // items the last launch handed to the simple simulator
+    int lanes = 32;                        // lanes per simulation (16 or 32)
+    int levels = 4;                        // saved DFS levels (items fix N - 1 - levels kernels)
+    bool disabled = false;                 // use the simple simulator only
+    int run_limit = 32;                    // cap on runs per simulation (tests force overflow)
 };
 
 // Makespans of all N! orders into d_out (if non-null) and the accumulators.

@@ -205,7 +205,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 __global__ void __launch_bounds__(kThreads)
 simple_kernel(const KoSet *__restrict__ d_set, const int8_t *__restrict__ perms,
-              const uint64_t *__restrict__ idx, unsigned long long first, long long count,
+              const uint64_t *__restrict__ idx, const unsigned long long *__restrict__ items,
+              unsigned long long span, unsigned long long first, long long count,
               int64_t *__restrict__ out, KoAccum *acc, void *scratch, size_t per_thread)
 {
     __shared__ KoSet sd;
@@ -225,7 +226,20 @@ simple_kernel(const KoSet *__restrict__ d_set, const int8_t *__restrict__ perms,
         if (j >= count) continue;
         int8_t perm[KO_MAX_KERNELS];
         bool ok = true;
-        if (perms) {
+        long long outpos = j;
+        if (items) {
+            // work-item list: item covers span consecutive indices, or one idx entry
+            const unsigned long long it = items[j / (long long)span];
+            if (idx) {
+                outpos = (long long)it;
+                ok = idx[it] < c_fact[n];
+                unrank(n, ok ? idx[it] : 0, perm);
+            } else {
+                const unsigned long long lehmer = it * span + (unsigned long long)(j % (long long)span);
+                outpos = (long long)lehmer;
+                unrank(n, lehmer, perm);
+            }
+        } else if (perms) {
             uint32_t seen = 0;
             for (int q = 0; q < n; q++) {
                 int v = perms[j * n + q];
@@ -234,10 +248,12 @@ simple_kernel(const KoSet *__restrict__ d_set, const int8_t *__restrict__ perms,
                 perm[q] = (int8_t)(v < 0 || v >= n ? 0 : v);
             }
         } else {
-            unrank(n, idx ? idx[j] : first + (unsigned long long)j, perm);
+            const unsigned long long k = idx ? idx[j] : first + (unsigned long long)j;
+            ok = k < c_fact[n];
+            unrank(n, ok ? k : 0, perm);
         }
         int64_t ms = ok ? simulate(sd, perm, st) : -1;
-        if (out) out[j] = ms;
+        if (out) out[outpos] = ms;
         if (ms < 0) { nf++; continue; }
         unsigned long long u = (unsigned long long)ms;
         lmin = u < lmin ? u : lmin;
@@ -310,9 +326,35 @@ cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_
     if (blocks > need) blocks = need;
     if (blocks < 1) return cudaErrorMemoryAllocation;
     if (blocks > 65535) blocks = 65535;
-    simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, perms, idx, first, count, out,
-                                                             acc, scratch, per);
+    simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, perms, idx, nullptr, 1, first,
+                                                             count, out, acc, scratch, per);
     return cudaGetLastError();
+}
+
+ko_status ko_simple_items(const KoSet &h, const KoSet *d_set, const uint64_t *idx,
+                          const unsigned long long *items, long long n_items, unsigned long long span,
+                          int64_t *out, KoAccum *acc, cudaStream_t stream)
+{
+    const long long count = n_items * (long long)span;
+    if (count <= 0) return KO_OK;
+    const size_t per = slab_bytes(h.S, h.Bk);
+    long long slots = (long long)((size_t(256) << 20) / per);
+    long long blocks = slots / kThreads;
+    const long long need = (count + kThreads - 1) / kThreads;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 65535) blocks = 65535;
+    void *scratch = nullptr;
+    if (cudaMalloc(&scratch, per * (size_t)blocks * kThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, nullptr, idx, items, span, 0,
+                                                             count, out, acc, scratch, per);
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(stream);
+    cudaFree(scratch);
+    return (e == cudaSuccess && e2 == cudaSuccess) ? KO_OK : KO_ERR_CUDA;
 }
 
 cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum *acc,

@@ -55,6 +55,8 @@ _SIGNATURES = {
     "ko_rank_order": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ko_rank),
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "ko_eval_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    "ko_last_fallback_items": (ctypes.c_int64, [ctypes.c_void_p]),
     "ko_destroy_gpu": (None, [ctypes.c_void_p]),
     "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "ko_last_error": (ctypes.c_int32, []),
@@ -174,6 +176,17 @@ def ko_eval_all(g, out, stream=None):
     return _check(lib().ko_eval_all(g, _ptr(out), _stream(stream)), "ko_eval_all")
 
 
+KO_OPT_LANES, KO_OPT_LEVELS, KO_OPT_SIMPLE_ONLY, KO_OPT_RUN_LIMIT = 1, 2, 3, 4
+
+
+def ko_set_option(g, key, value):
+    return _check(lib().ko_set_option(g, key, value), "ko_set_option")
+
+
+def ko_last_fallback_items(g):
+    return lib().ko_last_fallback_items(g)
+
+
 def ko_destroy_gpu(g):
     lib().ko_destroy_gpu(g)
 
@@ -225,6 +238,23 @@ class Gpu:
 
     def eval_all(self, out, stream=None):
         return ko_eval_all(self.h, out, stream=stream)
+
+    def set_option(self, key, value):
+        return ko_set_option(self.h, key, value)
+
+    def configure(self, lanes=None, levels=None, simple_only=None, run_limit=None):
+        if lanes is not None:
+            self.set_option(KO_OPT_LANES, lanes)
+        if levels is not None:
+            self.set_option(KO_OPT_LEVELS, levels)
+        if simple_only is not None:
+            self.set_option(KO_OPT_SIMPLE_ONLY, int(bool(simple_only)))
+        if run_limit is not None:
+            self.set_option(KO_OPT_RUN_LIMIT, run_limit)
+        return self
+
+    def last_fallback_items(self):
+        return ko_last_fallback_items(self.h)
 
     def n_orders(self):
         return math.factorial(self.n)

@@ -1,0 +1,113 @@
+"""GPU parity of the run-length, prefix-sharing simulator: every makespan must
+equal the oracle's (and the simple device simulator's) for every tuning knob
+setting, including forced hand-over of work items to the simple simulator."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_07983_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ko():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1511_07983_gb300 import build, ko as kmod
+    build.build()
+    torch.cuda.init()
+    return kmod
+
+
+def _all(g, n):
+    import torch
+    out = torch.empty(math.factorial(n), dtype=torch.int64, device="cuda")
+    g.eval_all(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("lanes", [16, 32])
+@pytest.mark.parametrize("levels", [0, 1, 3, 4, 6])
+def test_single8_all_orders_every_config(ko, lanes, levels):
+    s = synth.gen_set("single8")
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=40320)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=lanes, levels=levels)
+        assert np.array_equal(_all(g, 8), want)
+        assert g.last_fallback_items() == 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_sets_exhaustive(ko, seed):
+    # mixes of tiny and large N_SM, power-of-two and odd capacities, heavy smem
+    n = 3 + seed % 6
+    gpus = [(13, 65536, 49152, 64, 16), (148, 65536, 233472, 64, 32), (7, 32768, 49152, 48, 8),
+            (40, 65536, 98304, 64, 32)]
+    gpu = gpus[seed % len(gpus)]
+    caps = (32768, 32768) if seed % 3 else (3000, 7001)
+    s = synth.random_set(100 + seed, n, gpu=gpu, blk=(1, 5 * gpu[0]), c=(100, 30000),
+                         c_cap=caps[0], m_cap=caps[1])
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=math.factorial(n))
+    for lanes in (16, 32):
+        with ko.Gpu.from_set(s) as g:
+            g.configure(lanes=lanes)
+            got = _all(g, n)
+            assert np.array_equal(got, want), (lanes, int(np.argmax(got != want)))
+
+
+@pytest.mark.parametrize("run_limit", [1, 2, 3])
+def test_forced_handover_to_simple_simulator(ko, run_limit):
+    s = synth.gen_set("sets10", 2, n=7)
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=5040)
+    h = oracle.heuristic(s.gpu, s.kernels)
+    st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h),
+                                 makespans=want)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(run_limit=run_limit)
+        assert np.array_equal(_all(g, 7), want)
+        assert g.last_fallback_items() > 0
+        r, hist = g.rank_order(h, nbins=4096)
+    assert (r["min"], r["max"], r["n_better"], r["n_equal"], r["n_worse"]) == \
+        (st["min"], st["max"], st["n_better"], st["n_equal"], st["n_worse"])
+    assert np.array_equal(hist, st["hist"])
+
+
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_single12_index_sample(ko, lanes):
+    s = synth.gen_set("single12")
+    ids = synth.random_indices(77, math.factorial(12), 3000)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=lanes)
+        got = g.eval_orders(idx=ids)
+    assert np.array_equal(got, oracle.makespans_idx(s.gpu, s.kernels, idx=ids))
+
+
+def test_simple_and_fast_agree_on_sets10(ko):
+    s = synth.gen_set("sets10", 5)
+    with ko.Gpu.from_set(s) as g:
+        fast = _all(g, 10)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(simple_only=True)
+        simple = _all(g, 10)
+    assert np.array_equal(fast, simple)
+    ids = synth.random_indices(3, math.factorial(10), 3000).astype(np.int64)
+    assert np.array_equal(fast[ids], oracle.makespans_idx(s.gpu, s.kernels, idx=ids.astype(np.uint64)))
+
+
+@pytest.mark.parametrize("workload,count", [("batched", 40)])
+def test_batched_sets_exhaustive_small(ko, workload, count):
+    # every batched set with N <= 8 exhaustively against the oracle
+    checked = 0
+    for i in range(count):
+        s = synth.gen_set(workload, i)
+        if s.n > 8:
+            continue
+        want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=math.factorial(s.n))
+        with ko.Gpu.from_set(s) as g:
+            assert np.array_equal(_all(g, s.n), want), i
+        checked += 1
+    assert checked > 5

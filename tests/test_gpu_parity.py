@@ -197,3 +197,15 @@ def test_determinism(ko):
         a = g.eval_orders(idx=ids)
         b = g.eval_orders(idx=ids)
     assert np.array_equal(a, b)
+
+
+def test_out_of_range_index_is_invalid(ko):
+    s = synth.random_set(6, 5)
+    ids = np.array([0, 119, 120, 10 ** 12, 5], dtype=np.uint64)
+    with ko.Gpu.from_set(s) as g:
+        got = g.eval_orders(idx=ids)
+        g.configure(simple_only=True)
+        got_simple = g.eval_orders(idx=ids)
+    want = oracle.makespans_idx(s.gpu, s.kernels, idx=np.array([0, 119, 5], dtype=np.uint64))
+    assert got[2] == -1 and got[3] == -1 and got_simple[2] == -1 and got_simple[3] == -1
+    assert [got[0], got[1], got[4]] == want.tolist() == [got_simple[0], got_simple[1], got_simple[4]]
