@@ -173,6 +173,19 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
  * -1 for a NULL handle.  Informational: results are exact either way. */
 int64_t ko_last_fallback_items(const ko_gpu *g);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles, all threads).  Diagnostic counter for benchmarks. */
+int64_t ko_kernel_launches(void);
+
+/* Device time in milliseconds of the last run-length simulator launch on this
+ * handle, measured with CUDA events recorded on the launching stream around
+ * that launch; -1 if none. */
+double ko_last_sim_ms(const ko_gpu *g);
+
+/* Bytes this handle has copied host->device and device->host since it was
+ * created (inputs, staged buffers, results).  KO_ERR_ARG on NULL arguments. */
+ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h);
+
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);
 

@@ -1,6 +1,7 @@
 // libko C ABI: handle management, argument validation, staging of host
 // buffers, and dispatch to the simulator kernels.  See include/ko.h.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -11,6 +12,7 @@
 namespace {
 
 thread_local ko_status t_last_error = KO_OK;
+std::atomic<long long> g_launches{0};
 
 ko_status fail(ko_status s)
 {
@@ -52,6 +54,8 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
+void ko_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 struct ko_gpu {
     KoSet h{};
     bool frozen = false;       // kernels / capacities fixed after the first evaluation
@@ -65,6 +69,7 @@ struct ko_gpu {
     size_t stage_cap = 0;
     unsigned long long *d_hist = nullptr;
     int hist_cap = 0;
+    long long h2d = 0, d2h = 0;   // bytes copied by this handle
     KoFastState fast{};        // run-length simulator state (work list, overflow list)
 
     ~ko_gpu()
@@ -106,6 +111,7 @@ ko_status prepare(ko_gpu *g, cudaStream_t st)
     }
     if (cudaMemcpyAsync(g->d_set, &g->h, sizeof(KoSet), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return KO_ERR_CUDA;
+    g->h2d += sizeof(KoSet);
     return KO_OK;
 }
 
@@ -235,6 +241,7 @@ ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, i
     if (!in_dev) {
         if (cudaMemcpyAsync(stage, in, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return fail(KO_ERR_CUDA);
+        g->h2d += (long long)in_bytes;
         d_in = stage;
         stage += (in_bytes + 255) / 256 * 256;
     }
@@ -259,6 +266,7 @@ ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, i
         if (cudaMemcpyAsync(makespan_out, d_out, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess)
             return fail(KO_ERR_CUDA);
+        g->d2h += (long long)sizeof(int64_t) * n;
     }
     if (!in_dev || !out_dev) {
         if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
@@ -296,12 +304,14 @@ ko_status makespan_of(ko_gpu *g, const int32_t *order, int64_t *m, cudaStream_t 
     int8_t *d_perm = (int8_t *)g->d_stage;
     int64_t *d_m = (int64_t *)((char *)g->d_stage + 256);
     if (cudaMemcpyAsync(d_perm, perm, N, cudaMemcpyHostToDevice, st) != cudaSuccess) return KO_ERR_CUDA;
+    g->h2d += N;
     if ((s = simple_scratch(g, 1))) return s;
     if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, d_perm, nullptr, 0, 1, d_m, nullptr,
                                          g->scratch, g->scratch_bytes, st))))
         return s;
     if (cudaMemcpyAsync(m, d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return KO_ERR_CUDA;
+    g->d2h += sizeof(int64_t);
     if (cudaStreamSynchronize(st) != cudaSuccess) return KO_ERR_CUDA;
     return KO_OK;
 }
@@ -369,13 +379,17 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
             return fail(KO_ERR_CUDA);
         if ((s = check_cuda(ko_launch_histogram(g->d_ms, total, g->d_acc, dh, nbins, st))))
             return fail(s);
-        if (!hist_dev && cudaMemcpyAsync(hist, dh, sizeof(unsigned long long) * nbins,
-                                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            return fail(KO_ERR_CUDA);
+        if (!hist_dev) {
+            if (cudaMemcpyAsync(hist, dh, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost,
+                                st) != cudaSuccess)
+                return fail(KO_ERR_CUDA);
+            g->d2h += (long long)sizeof(unsigned long long) * nbins;
+        }
     }
     KoAccum acc;
     if (cudaMemcpyAsync(&acc, g->d_acc, sizeof(KoAccum), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(KO_ERR_CUDA);
+    g->d2h += sizeof(KoAccum);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
     if (acc.failed) return fail(KO_ERR_STATE);
     out->min = (int64_t)acc.min;
@@ -439,5 +453,17 @@ const char *ko_status_str(ko_status s)
 }
 
 ko_status ko_last_error(void) { return t_last_error; }
+
+int64_t ko_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+double ko_last_sim_ms(const ko_gpu *g) { return g ? g->fast.last_ms : -1.0; }
+
+ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h)
+{
+    if (!g || !h2d || !d2h) return fail(KO_ERR_ARG);
+    *h2d = g->h2d + g->fast.h2d;
+    *d2h = g->d2h + g->fast.d2h;
+    return ok();
+}
 
 }  // extern "C"

@@ -596,6 +596,7 @@ cudaError_t launch(const FastArgs &a, cudaStream_t st)
     if (blocks > blocks_needed) blocks = blocks_needed;
     if (blocks < 1) blocks = 1;
     fast_kernel<LANES><<<(unsigned)blocks, kThreads, smem, st>>>(a);
+    ko_count_launch();
     return cudaGetLastError();
 }
 
@@ -617,15 +618,22 @@ ko_status run_fast(KoFastState *fs, const KoSet &h, const KoSet *d_set, FastArgs
     a.ov_list = fb->ov_list;
     a.ov_cap = kOvCap;
     a.run_limit = fs->run_limit;
+    if (!fs->ev0 && (cudaEventCreate(&fs->ev0) != cudaSuccess || cudaEventCreate(&fs->ev1) != cudaSuccess))
+        return KO_ERR_CUDA;
+    cudaEventRecord(fs->ev0, st);
     cudaError_t e = fs->lanes == 16 ? launch<16>(a, st) : launch<32>(a, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_CUDA;
     }
+    cudaEventRecord(fs->ev1, st);
     unsigned long long cnt = 0;
     if (cudaMemcpyAsync(&cnt, &fb->ov_count, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return KO_ERR_CUDA;
+    fs->d2h += sizeof(cnt);
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, fs->ev0, fs->ev1) == cudaSuccess) fs->last_ms = ms;
     fs->last_overflow = cnt;
     if (cnt == 0) return KO_OK;
     if (cnt > kOvCap) return 1;  // too many abandoned items: caller redoes everything
@@ -673,6 +681,9 @@ ko_status ko_fast_eval_idx(KoFastState *fs, const KoSet &h, const KoSet *d_set,
 
 void ko_fast_release(KoFastState *fs)
 {
+    if (fs->ev0) cudaEventDestroy(fs->ev0);
+    if (fs->ev1) cudaEventDestroy(fs->ev1);
+    fs->ev0 = fs->ev1 = nullptr;
     cudaFree(fs->buf);
     fs->buf = nullptr;
     fs->cap = 0;

@@ -12,6 +12,9 @@ struct KoFastState {
     int levels = 4;                        // saved DFS levels (items fix N - 1 - levels kernels)
     bool disabled = false;                 // use the simple simulator only
     int run_limit = 32;                    // cap on runs per simulation (tests force overflow)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last fast-kernel launch
+    double last_ms = -1.0;
+    long long h2d = 0, d2h = 0;            // bytes copied by the fast path
 };
 
 // Makespans of all N! orders into d_out (if non-null) and the accumulators.

@@ -31,6 +31,9 @@ struct KoAccum {
     unsigned long long failed;   // simulations that could not finish
 };
 
+// Count of kernels launched by the library (ko_kernel_launches).
+void ko_count_launch(int n = 1);
+
 // ------------------------------------------------------------------ launchers
 // All launchers are asynchronous on `stream` and return the launch status.
 

@@ -328,6 +328,7 @@ cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_
     if (blocks > 65535) blocks = 65535;
     simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, perms, idx, nullptr, 1, first,
                                                              count, out, acc, scratch, per);
+    ko_count_launch();
     return cudaGetLastError();
 }
 
@@ -351,6 +352,7 @@ ko_status ko_simple_items(const KoSet &h, const KoSet *d_set, const uint64_t *id
     }
     simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, nullptr, idx, items, span, 0,
                                                              count, out, acc, scratch, per);
+    ko_count_launch();
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(stream);
     cudaFree(scratch);
@@ -370,11 +372,13 @@ cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum 
         if (e != cudaSuccess) return e;
     }
     hist_kernel<<<(unsigned)blocks, kHistThreads, smem, stream>>>(ms, count, acc, hist, nbins);
+    ko_count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t ko_launch_accum_reset(KoAccum *acc, int count, cudaStream_t stream)
 {
     accum_reset_kernel<<<(count + 127) / 128, 128, 0, stream>>>(acc, count);
+    ko_count_launch();
     return cudaGetLastError();
 }

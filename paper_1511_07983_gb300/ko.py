@@ -57,6 +57,10 @@ _SIGNATURES = {
     "ko_eval_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ko_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_last_fallback_items": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ko_kernel_launches": (ctypes.c_int64, []),
+    "ko_last_sim_ms": (ctypes.c_double, [ctypes.c_void_p]),
+    "ko_transfer_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "ko_destroy_gpu": (None, [ctypes.c_void_p]),
     "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "ko_last_error": (ctypes.c_int32, []),
@@ -187,6 +191,20 @@ def ko_last_fallback_items(g):
     return lib().ko_last_fallback_items(g)
 
 
+def ko_kernel_launches():
+    return lib().ko_kernel_launches()
+
+
+def ko_last_sim_ms(g):
+    return lib().ko_last_sim_ms(g)
+
+
+def ko_transfer_bytes(g):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ko_transfer_bytes(g, ctypes.byref(a), ctypes.byref(b)), "ko_transfer_bytes")
+    return a.value, b.value
+
+
 def ko_destroy_gpu(g):
     lib().ko_destroy_gpu(g)
 
@@ -255,6 +273,12 @@ class Gpu:
 
     def last_fallback_items(self):
         return ko_last_fallback_items(self.h)
+
+    def last_sim_ms(self):
+        return ko_last_sim_ms(self.h)
+
+    def transfer_bytes(self):
+        return ko_transfer_bytes(self.h)
 
     def n_orders(self):
         return math.factorial(self.n)
