@@ -52,6 +52,14 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Small per-call device records of a handle.
+struct Meta {
+    KoChunk chunk[2];                 // [0] heuristic order (mode 2), [1] the main work
+    long long ref;                    // reference makespan written by the heuristic pass
+    long long pad;
+    int8_t perm[KO_MAX_KERNELS + 8];  // heuristic / ranked order
+};
+
 }  // namespace
 
 void ko_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -70,12 +78,16 @@ struct ko_gpu {
     unsigned long long *d_hist = nullptr;
     int hist_cap = 0;
     long long h2d = 0, d2h = 0;   // bytes copied by this handle
+    Meta *d_meta = nullptr;       // chunk lists, heuristic order, reference makespan (device)
+    Meta h_meta{};
     KoFastState fast{};        // run-length simulator state (work list, overflow list)
+    bool fast_pending = false; // an asynchronous run-length launch has not been inspected yet
 
     ~ko_gpu()
     {
         cudaFree(d_set); cudaFree(d_acc); cudaFree(scratch); cudaFree(d_ms); cudaFree(d_stage);
         cudaFree(d_hist);
+        cudaFree(d_meta);
         ko_fast_release(&fast);
     }
 };
@@ -129,6 +141,73 @@ ko_status check_cuda(cudaError_t e)
     if (e == cudaSuccess) return KO_OK;
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? KO_ERR_NOMEM : KO_ERR_CUDA;
+}
+
+bool fast_ok(const ko_gpu *g) { return !g->fast.disabled && ko_fast_applicable(g->h); }
+
+ko_status upload_meta(ko_gpu *g, cudaStream_t st)
+{
+    if (!g->d_meta && cudaMalloc(&g->d_meta, sizeof(Meta)) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    if (cudaMemcpyAsync(g->d_meta, &g->h_meta, sizeof(Meta), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return KO_ERR_CUDA;
+    g->h2d += sizeof(Meta);
+    return KO_OK;
+}
+
+KoWork work_for(ko_gpu *g, int chunk)
+{
+    KoWork w{};
+    w.sets = g->d_set;
+    w.chunks = &g->d_meta->chunk[chunk];
+    w.nchunks = 1;
+    w.n_items = g->h_meta.chunk[chunk].count;
+    w.levels = 1;
+    return w;
+}
+
+// Exhaustive chunk (all N! orders as prefix items) into h_meta.chunk[1].
+void exhaustive_chunk(ko_gpu *g, KoWork *w_levels)
+{
+    const int N = g->h.n;
+    const int d0 = ko_fast_d0(g->fast, N);
+    KoChunk &c = g->h_meta.chunk[1];
+    c = KoChunk{};
+    c.first = 0;
+    c.count = kFactorial[N] / kFactorial[N - d0];
+    c.set = 0;
+    c.d0 = d0;
+    c.mode = 0;
+    *w_levels = KoWork{};
+    w_levels->levels = N - 1 - d0 > 0 ? N - 1 - d0 : 1;
+}
+
+ko_status fast_launch_timed(ko_gpu *g, const KoWork &w, cudaStream_t st)
+{
+    KoFastState &fs = g->fast;
+    if (!fs.ev0 && (cudaEventCreate(&fs.ev0) != cudaSuccess || cudaEventCreate(&fs.ev1) != cudaSuccess))
+        return KO_ERR_CUDA;
+    cudaEventRecord(fs.ev0, st);
+    ko_status s = ko_fast_launch(&fs, w, ko_slab_bytes(g->h.S, g->h.Bk), st);
+    cudaEventRecord(fs.ev1, st);
+    return s;
+}
+
+// After a synchronise: read the event time and the abandoned-item count.
+ko_status fast_after_sync(ko_gpu *g)
+{
+    KoFastState &fs = g->fast;
+    float ms = -1.0f;
+    if (fs.ev0 && cudaEventElapsedTime(&ms, fs.ev0, fs.ev1) == cudaSuccess) fs.last_ms = ms;
+    cudaGetLastError();
+    unsigned long long cnt = 0;
+    const unsigned long long *dc = ko_fast_overflow_counter(&fs);
+    if (dc && cudaMemcpy(&cnt, dc, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess) return KO_ERR_CUDA;
+    fs.d2h += sizeof(cnt);
+    fs.last_overflow = cnt;
+    return cnt > (1ull << 20) ? KO_ERR_STATE : KO_OK;
 }
 
 }  // namespace
@@ -246,20 +325,26 @@ ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, i
         stage += (in_bytes + 255) / 256 * 256;
     }
     int64_t *d_out = out_dev ? makespan_out : (int64_t *)stage;
-    if (idx) {
-        // Lehmer-index lists go to the run-length simulator when it applies.
-        s = ko_fast_eval_idx(&g->fast, g->h, g->d_set, (const uint64_t *)d_in, n, d_out, st);
-        if (s < 0) return fail(s);
-        if (s == 1) {
-            if ((s = simple_scratch(g, n))) return fail(s);
-            if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, (const uint64_t *)d_in, 0,
-                                                 n, d_out, nullptr, g->scratch, g->scratch_bytes, st))))
-                return fail(s);
-        }
+    bool used_fast = false;
+    if (fast_ok(g)) {
+        KoChunk &c = g->h_meta.chunk[1];
+        c = KoChunk{};
+        c.count = n;
+        c.d0 = N;
+        c.mode = idx ? 1 : 2;
+        if ((s = upload_meta(g, st))) return fail(s);
+        KoWork w = work_for(g, 1);
+        w.idx = idx ? (const uint64_t *)d_in : nullptr;
+        w.perms = idx ? nullptr : (const int8_t *)d_in;
+        w.out = d_out;
+        if ((s = fast_launch_timed(g, w, st))) return fail(s);
+        used_fast = true;
+        g->fast_pending = true;
     } else {
         if ((s = simple_scratch(g, n))) return fail(s);
-        if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, (const int8_t *)d_in, nullptr, 0, n,
-                                             d_out, nullptr, g->scratch, g->scratch_bytes, st))))
+        if ((s = check_cuda(ko_launch_simple(g->d_set, g->h, idx ? nullptr : (const int8_t *)d_in,
+                                             idx ? (const uint64_t *)d_in : nullptr, 0, n, d_out,
+                                             nullptr, g->scratch, g->scratch_bytes, st))))
             return fail(s);
     }
     if (!out_dev) {
@@ -270,6 +355,10 @@ ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, i
     }
     if (!in_dev || !out_dev) {
         if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
+        if (used_fast) {
+            g->fast_pending = false;
+            if ((s = fast_after_sync(g))) return fail(s);
+        }
     }
     return ok();
 }
@@ -278,20 +367,27 @@ ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, i
 
 namespace {
 
-// All N! makespans into d_out (device) and the accumulators, on `st`.
-ko_status exhaustive(ko_gpu *g, int64_t *d_out, KoAccum *d_acc, cudaStream_t st)
+// All N! makespans into d_out (device, nullable) and the accumulator, on
+// `st`; with `refs` the counts compare against *refs (device).
+ko_status exhaustive(ko_gpu *g, int64_t *d_out, KoAccum *d_acc, long long *refs, cudaStream_t st)
 {
     const int64_t total = kFactorial[g->h.n];
     ko_status s = check_cuda(ko_launch_accum_reset(d_acc, 1, st));
     if (s) return s;
-    s = ko_fast_exhaustive(&g->fast, g->h, g->d_set, d_out, d_acc, st);
-    if (s == 1) {  // run-length simulator does not apply: simple simulator over all indices
-        if ((s = check_cuda(ko_launch_accum_reset(d_acc, 1, st)))) return s;
-        if ((s = simple_scratch(g, total))) return s;
-        s = check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, nullptr, 0, total, d_out, d_acc,
-                                        g->scratch, g->scratch_bytes, st));
+    if (fast_ok(g)) {
+        KoWork lv;
+        exhaustive_chunk(g, &lv);
+        if ((s = upload_meta(g, st))) return s;
+        KoWork w = work_for(g, 1);
+        w.levels = lv.levels;
+        w.refs = refs;
+        w.accs = d_acc;
+        w.out = d_out;
+        return fast_launch_timed(g, w, st);
     }
-    return s;
+    if ((s = simple_scratch(g, total))) return s;
+    return check_cuda(ko_launch_simple(g->d_set, g->h, nullptr, nullptr, 0, total, d_out, d_acc,
+                                       g->scratch, g->scratch_bytes, st));
 }
 
 ko_status makespan_of(ko_gpu *g, const int32_t *order, int64_t *m, cudaStream_t st)
@@ -329,7 +425,8 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream)
     g->h.ref_makespan = 0;
     ko_status s = prepare(g, st);
     if (s) return fail(s);
-    if ((s = exhaustive(g, makespans_out, g->d_acc, st))) return fail(s);
+    if ((s = exhaustive(g, makespans_out, g->d_acc, nullptr, st))) return fail(s);
+    g->fast_pending = fast_ok(g);
     return ok();
 }
 
@@ -351,17 +448,43 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
     } else {
         ko_heuristic_host(g->h, ord.data());
     }
+    const int64_t total = kFactorial[N];
     g->h.ref_makespan = 0;
     ko_status s = prepare(g, st);
     if (s) return fail(s);
-    int64_t mh = 0;
-    if ((s = makespan_of(g, ord.data(), &mh, st))) return fail(s);
-    if (mh < 0) return fail(KO_ERR_STATE);
-    g->h.ref_makespan = mh;
-    if ((s = prepare(g, st))) return fail(s);
-    const int64_t total = kFactorial[N];
     if ((s = grow((void **)&g->d_ms, &g->ms_cap, sizeof(int64_t) * total))) return fail(s);
-    if ((s = exhaustive(g, g->d_ms, g->d_acc, st))) return fail(s);
+    int64_t mh = 0;
+    const bool fast = fast_ok(g);
+    if (fast) {
+        // pass 1: makespan of the ranked order into d_meta->ref (device);
+        // pass 2: all N! orders, counted against that reference
+        KoChunk &c0 = g->h_meta.chunk[0];
+        c0 = KoChunk{};
+        c0.count = 1;
+        c0.d0 = N;
+        c0.mode = 2;
+        for (int i = 0; i < N; i++) g->h_meta.perm[i] = (int8_t)ord[i];
+        KoWork lv;
+        exhaustive_chunk(g, &lv);
+        if ((s = upload_meta(g, st))) return fail(s);
+        KoWork w0 = work_for(g, 0);
+        w0.perms = g->d_meta->perm;
+        w0.out = (int64_t *)&g->d_meta->ref;
+        if ((s = ko_fast_launch(&g->fast, w0, ko_slab_bytes(g->h.S, g->h.Bk), st))) return fail(s);
+        if ((s = check_cuda(ko_launch_accum_reset(g->d_acc, 1, st)))) return fail(s);
+        KoWork w1 = work_for(g, 1);
+        w1.levels = lv.levels;
+        w1.refs = &g->d_meta->ref;
+        w1.accs = g->d_acc;
+        w1.out = g->d_ms;
+        if ((s = fast_launch_timed(g, w1, st))) return fail(s);
+    } else {
+        if ((s = makespan_of(g, ord.data(), &mh, st))) return fail(s);
+        if (mh < 0) return fail(KO_ERR_STATE);
+        g->h.ref_makespan = mh;
+        if ((s = prepare(g, st))) return fail(s);
+        if ((s = exhaustive(g, g->d_ms, g->d_acc, nullptr, st))) return fail(s);
+    }
     if (hist) {
         if (g->hist_cap < nbins) {
             cudaFree(g->d_hist);
@@ -390,8 +513,14 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
     if (cudaMemcpyAsync(&acc, g->d_acc, sizeof(KoAccum), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(KO_ERR_CUDA);
     g->d2h += sizeof(KoAccum);
+    if (fast) {
+        if (cudaMemcpyAsync(&mh, &g->d_meta->ref, sizeof(mh), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+        g->d2h += sizeof(mh);
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
-    if (acc.failed) return fail(KO_ERR_STATE);
+    if (fast && (s = fast_after_sync(g))) return fail(s);
+    if (acc.failed || mh < 0) return fail(KO_ERR_STATE);
     out->min = (int64_t)acc.min;
     out->max = (int64_t)acc.max;
     out->makespan = mh;
@@ -432,7 +561,17 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
     return ok();
 }
 
-int64_t ko_last_fallback_items(const ko_gpu *g) { return g ? (int64_t)g->fast.last_overflow : -1; }
+int64_t ko_last_fallback_items(const ko_gpu *g)
+{
+    if (!g) return -1;
+    ko_gpu *m = const_cast<ko_gpu *>(g);
+    if (m->fast_pending) {  // asynchronous launch: wait for it, then read its counters
+        cudaDeviceSynchronize();
+        fast_after_sync(m);
+        m->fast_pending = false;
+    }
+    return (int64_t)g->fast.last_overflow;
+}
 
 void ko_destroy_gpu(ko_gpu *g) { delete g; }
 
@@ -456,7 +595,12 @@ ko_status ko_last_error(void) { return t_last_error; }
 
 int64_t ko_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
-double ko_last_sim_ms(const ko_gpu *g) { return g ? g->fast.last_ms : -1.0; }
+double ko_last_sim_ms(const ko_gpu *g)
+{
+    if (!g) return -1.0;
+    ko_last_fallback_items(g);
+    return g->fast.last_ms;
+}
 
 ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h)
 {

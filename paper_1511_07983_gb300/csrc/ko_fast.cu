@@ -33,13 +33,14 @@
 
 namespace {
 
-constexpr int kG = 8;                       // group slots per run
+constexpr int kG = 8;                       // group slots per run (first pass)
+constexpr int kGWide = 16;                  // group slots per run (pass over abandoned items)
 constexpr uint32_t kPend = 1u << 15;        // group started in the open burst
 constexpr uint32_t kValid = 1u << 16;       // slot holds a group
 // group word: kernel id (bits 0-4) | blocks per SM (bits 8-13) | kPend | kValid
 
 constexpr int kMaxLevels = 6;               // saved DFS levels per segment
-constexpr int kStateWords = 8 + 2 * kG;     // per-lane registers saved per level
+__host__ __device__ constexpr int state_words(int G) { return 8 + 2 * G; }  // per-lane words saved per level
 constexpr int kThreads = 128;
 
 __constant__ unsigned long long c_fact[21] = {
@@ -52,26 +53,9 @@ struct SetConst {
     int n, S, R, Sh, W, Bk;
     long long ccap, mcap;
     int cshift, mshift;
-    long long ref;
     int total_blocks;
     int r[KO_MAX_KERNELS], s[KO_MAX_KERNELS], w[KO_MAX_KERNELS], b[KO_MAX_KERNELS];
     int c[KO_MAX_KERNELS], m[KO_MAX_KERNELS];
-};
-
-struct FastArgs {
-    const KoSet *set;
-    int mode;                   // 0 = exhaustive over prefix items, 1 = explicit index list
-    int d0;                     // prefix depth of a work item (mode 0)
-    long long n_items;
-    const uint64_t *idx;        // mode 1
-    int64_t *out;               // makespans (nullable in mode 0)
-    KoAccum *acc;               // nullable
-    unsigned long long *counter;     // work counter
-    unsigned long long *ov_count;    // abandoned items
-    unsigned long long *ov_list;
-    unsigned long long ov_cap;
-    int levels;                 // saved levels per segment
-    int run_limit;              // runs a segment may hold (<= LANES)
 };
 
 template <int LANES>
@@ -89,16 +73,19 @@ __device__ __forceinline__ unsigned seg_ballot(const Seg<LANES> &sg, bool pred)
 }
 
 // Per-lane run state, held in registers (all array indices are compile-time).
+template <int G>
 struct Run {
     int beg, cnt, ur, us, uw, ub, sc, sm;
-    uint32_t gk[kG];
-    uint32_t ge[kG];
+    uint32_t gk[G];
+    uint32_t ge[G];
 };
 
-template <int LANES>
+template <int LANES, int G>
 struct Sim {
+    static constexpr int kG = G;
+    static constexpr int kStateWords = state_words(G);
     Seg<LANES> sg;
-    Run run;
+    Run<G> run;
     long long t;     // clock (segment-uniform)
     int p;           // round-robin pointer
     int nruns;
@@ -373,20 +360,23 @@ struct Sim {
     }
 };
 
-__device__ void load_const(SetConst &K, const KoSet *d)
+// Segment-cooperative load of one set's constants into shared memory.
+template <int LANES>
+__device__ void load_set(SetConst &K, const KoSet *d, const Seg<LANES> &sg)
 {
-    if (threadIdx.x == 0) {
+    int nb = 0;
+    for (int i = sg.lane; i < KO_MAX_KERNELS; i += LANES) {
+        const KoKern kk = d->k[i];
+        K.r[i] = kk.r; K.s[i] = kk.s; K.w[i] = kk.w; K.b[i] = kk.b; K.c[i] = kk.c; K.m[i] = kk.m;
+        if (i < d->n) nb += kk.b;
+    }
+    nb = (int)__reduce_add_sync(sg.mask, (unsigned)nb);
+    if (sg.lane == 0) {
         K.n = d->n; K.S = d->S; K.R = d->R; K.Sh = d->Sh; K.W = d->W; K.Bk = d->Bk;
         K.ccap = d->ccap; K.mcap = d->mcap; K.cshift = d->cshift; K.mshift = d->mshift;
-        K.ref = d->ref_makespan;
-        int tb = 0;
-        for (int i = 0; i < d->n; i++) tb += d->k[i].b;
-        K.total_blocks = tb;
+        K.total_blocks = nb;
     }
-    for (int i = threadIdx.x; i < KO_MAX_KERNELS; i += blockDim.x) {
-        K.r[i] = d->k[i].r; K.s[i] = d->k[i].s; K.w[i] = d->k[i].w;
-        K.b[i] = d->k[i].b; K.c[i] = d->k[i].c; K.m[i] = d->k[i].m;
-    }
+    __syncwarp(sg.mask);
 }
 
 // first `depth` kernels of the lexicographic permutation with Lehmer index k
@@ -405,76 +395,131 @@ __device__ void lehmer_prefix(int n, unsigned long long k, int depth, int8_t *pe
     }
 }
 
-template <int LANES>
-__global__ void __launch_bounds__(kThreads)
-fast_kernel(FastArgs a)
+__device__ __forceinline__ int find_chunk(const KoChunk *chunks, int nchunks, long long item)
 {
-    __shared__ SetConst K;
-    extern __shared__ int stack_mem[];
-    load_const(K, a.set);
-    __syncthreads();
+    int lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunks[mid].first <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
+// Per-segment running statistics of the set being worked on.
+struct SegStats {
+    int set = -1;
+    unsigned long long mn = ~0ull, mx = 0, nb = 0, ne = 0, nw = 0;
+    __device__ void flush(KoAccum *accs)
+    {
+        if (set >= 0 && accs) {
+            KoAccum *a = accs + set;
+            if (mn != ~0ull) atomicMin(&a->min, mn);
+            if (mx) atomicMax(&a->max, mx);
+            if (nb) atomicAdd(&a->n_better, nb);
+            if (ne) atomicAdd(&a->n_equal, ne);
+            if (nw) atomicAdd(&a->n_worse, nw);
+        }
+        mn = ~0ull; mx = 0; nb = ne = nw = 0;
+    }
+};
+
+template <int LANES, int G>
+__global__ void __launch_bounds__(kThreads)
+fast_kernel(KoWork a)
+{
+    constexpr int kStateWords = state_words(G);
     constexpr int kSegs = kThreads / LANES;
-    Sim<LANES> sim;
+    __shared__ SetConst Ks[kSegs];
+    extern __shared__ int stack_mem[];
+
+    Sim<LANES, G> sim;
     const int seg = threadIdx.x / LANES;
     sim.sg.lane = threadIdx.x % LANES;
     sim.run_limit = a.run_limit < LANES ? a.run_limit : LANES;
     sim.sg.mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
     const int level_words = kStateWords * LANES + 4;
     int *stack = stack_mem + seg * a.levels * level_words;
-    (void)kSegs;
-
-    const int n = K.n;
-    const long long ref = K.ref;
-    unsigned long long smin = ~0ull, smax = 0, sb = 0, se = 0, sw = 0;
+    SetConst &K = Ks[seg];
+    int loaded = -1;
+    SegStats st;    // meaningful on lane 0
 
     for (;;) {
         unsigned long long item = 0;
-        if (sim.sg.lane == 0) item = atomicAdd(a.counter, 1ull);
+        if (sim.sg.lane == 0) {
+            item = atomicAdd(a.counter, 1ull);
+            if (a.item_list) {  // pass over items a previous pass abandoned
+                const unsigned long long cnt = *a.item_count < a.ov_cap ? *a.item_count : a.ov_cap;
+                item = item < cnt ? a.item_list[item] : ~0ull;
+            }
+        }
         item = __shfl_sync(sim.sg.mask, item, 0, LANES);
         if (item >= (unsigned long long)a.n_items) break;
+        const KoChunk ch = a.chunks[find_chunk(a.chunks, a.nchunks, (long long)item)];
+        if (ch.set != loaded) {
+            load_set<LANES>(K, a.sets + ch.set, sim.sg);
+            loaded = ch.set;
+        }
+        if (sim.sg.lane == 0 && st.set != ch.set) {
+            st.flush(a.accs);
+            st.set = ch.set;
+        }
+        const int n = K.n;
+        const long long ref = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
+        const long long local = (long long)item - ch.first;
 
         int8_t perm[KO_MAX_KERNELS];
-        uint32_t used;
+        uint32_t used = 0;
         int d0;
-        unsigned long long base;
-        if (a.mode == 1) {
+        long long outpos;
+        bool valid = true;
+        if (ch.mode == 1) {
             d0 = n;
-            base = item;
-            const unsigned long long k = a.idx[item];
-            if (k >= c_fact[n]) {  // not a Lehmer index of this set
-                if (sim.sg.lane == 0 && a.out) a.out[base] = -1;
-                continue;
+            outpos = ch.out_off + local;
+            const unsigned long long k = a.idx[ch.list_off + local];
+            valid = k < c_fact[n];
+            if (valid) lehmer_prefix(n, k, n, perm, used);
+        } else if (ch.mode == 2) {
+            d0 = n;
+            outpos = ch.out_off + local;
+            const int8_t *row = a.perms + (ch.list_off + local) * n;
+            for (int j = 0; j < n; j++) {
+                const int v = row[j];
+                if (v < 0 || v >= n || ((used >> v) & 1u)) { valid = false; break; }
+                perm[j] = (int8_t)v;
+                used |= 1u << v;
             }
-            lehmer_prefix(n, k, n, perm, used);
         } else {
-            d0 = a.d0;
-            base = item * c_fact[n - d0];
+            d0 = ch.d0;
+            const unsigned long long base = (unsigned long long)local * c_fact[n - d0];
+            outpos = ch.out_off + (long long)base;
             lehmer_prefix(n, base, d0, perm, used);
+        }
+        if (!valid) {
+            if (sim.sg.lane == 0 && a.out) a.out[outpos] = -1;
+            continue;
         }
         sim.init(K);
         for (int j = 0; j < d0 && !sim.fail; j++) sim.place_kernel(K, perm[j]);
 
         unsigned long long imin = ~0ull, imax = 0, ib = 0, ie = 0, iw = 0;
-        unsigned long long leaf = 0;
+        long long leaf = 0;
         if (d0 == n) {
             if (!sim.fail) {
                 const long long ms = sim.finish(K);
                 if (sim.sg.lane == 0) {
-                    if (a.out) a.out[base] = ms;
+                    if (a.out) a.out[outpos] = ms;
                     imin = imax = (unsigned long long)ms;
                     ib = ms < ref; ie = ms == ref; iw = ms > ref;
                 }
             }
         } else {
-            // lexicographic DFS below the prefix
+            // lexicographic DFS below the prefix; node states saved per depth
             int depth = d0;
             int next[KO_MAX_KERNELS + 1];
             next[depth] = 0;
             bool first_child = true;
             if (!sim.fail && n - depth >= 2) sim.save(stack + (depth - d0) * level_words);
             while (!sim.fail) {
-                // next unused kernel id >= next[depth]
                 const uint32_t avail = ~used & ((1u << n) - 1u) & ~((1u << next[depth]) - 1u);
                 if (avail == 0) {
                     if (depth == d0) break;
@@ -494,7 +539,7 @@ fast_kernel(FastArgs a)
                 if (depth + 1 == n) {
                     const long long ms = sim.finish(K);
                     if (sim.sg.lane == 0) {
-                        if (a.out) a.out[base + leaf] = ms;
+                        if (a.out) a.out[outpos + leaf] = ms;
                         const unsigned long long u = (unsigned long long)ms;
                         imin = u < imin ? u : imin;
                         imax = u > imax ? u : imax;
@@ -517,37 +562,51 @@ fast_kernel(FastArgs a)
                 const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
                 if (slot < a.ov_cap) a.ov_list[slot] = item;
             }
-        } else {
-            smin = imin < smin ? imin : smin;
-            smax = imax > smax ? imax : smax;
-            sb += ib; se += ie; sw += iw;
+        } else if (sim.sg.lane == 0) {
+            st.mn = imin < st.mn ? imin : st.mn;
+            st.mx = imax > st.mx ? imax : st.mx;
+            st.nb += ib; st.ne += ie; st.nw += iw;
         }
     }
-    if (a.acc && sim.sg.lane == 0) {
-        if (smin != ~0ull) atomicMin(&a.acc->min, smin);
-        if (smax) atomicMax(&a.acc->max, smax);
-        if (sb) atomicAdd(&a.acc->n_better, sb);
-        if (se) atomicAdd(&a.acc->n_equal, se);
-        if (sw) atomicAdd(&a.acc->n_worse, sw);
-    }
+    if (sim.sg.lane == 0) st.flush(a.accs);
 }
 
 // Device buffer layout inside KoFastState::buf.
 struct FastBuf {
-    unsigned long long counter, ov_count, pad[6];
-    unsigned long long ov_list[1];
+    unsigned long long counter[2], ov_count[2], fb_counter, pad[3];
+    unsigned long long ov_list[1];   // kOvCap entries per pass
 };
 
 constexpr unsigned long long kOvCap = 1 << 20;
+constexpr size_t kFallbackScratch = size_t(256) << 20;
 
-unsigned long long c_fact_host(int n)
+
+template <int LANES, int G>
+cudaError_t launch(const KoWork &a, cudaStream_t st)
 {
-    unsigned long long f = 1;
-    for (int i = 2; i <= n; i++) f *= (unsigned long long)i;
-    return f;
+    const int level_words = state_words(G) * LANES + 4;
+    const size_t smem = sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
+    cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES, G>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
+    const long long blocks_needed = (work + kThreads / LANES - 1) / (kThreads / LANES);
+    if (blocks > blocks_needed) blocks = blocks_needed;
+    if (blocks < 1) blocks = 1;
+    fast_kernel<LANES, G><<<(unsigned)blocks, kThreads, smem, st>>>(a);
+    ko_count_launch();
+    return cudaGetLastError();
 }
 
-bool applicable(const KoSet &h)
+}  // namespace
+
+bool ko_fast_applicable(const KoSet &h)
 {
     if (h.n < 1) return false;
     int64_t cmax = 0, mmax = 0;
@@ -555,128 +614,85 @@ bool applicable(const KoSet &h)
         cmax = h.k[i].c > cmax ? h.k[i].c : cmax;
         mmax = h.k[i].m > mmax ? h.k[i].m : mmax;
     }
-    // every duration must stay below 2^31 for the modular end times
     const __int128 sc = (__int128)h.Bk * cmax, sm = (__int128)h.Bk * mmax;
     const __int128 dc = ((__int128)cmax * (sc > h.ccap ? sc : h.ccap) + h.ccap - 1) / h.ccap;
     const __int128 dm = ((__int128)mmax * (sm > h.mcap ? sm : h.mcap) + h.mcap - 1) / h.mcap;
     return dc < ((__int128)1 << 31) && dm < ((__int128)1 << 31);
 }
 
-ko_status ensure_buf(KoFastState *fs)
+int ko_fast_d0(const KoFastState &fs, int n)
 {
-    const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * kOvCap;
-    if (fs->cap >= need) return KO_OK;
-    cudaFree(fs->buf);
-    fs->buf = nullptr;
-    fs->cap = 0;
-    if (cudaMalloc(&fs->buf, need) != cudaSuccess) {
-        cudaGetLastError();
-        return KO_ERR_NOMEM;
+    int levels = fs.levels < kMaxLevels ? fs.levels : kMaxLevels;
+    const int d0 = n - 1 - levels;
+    return d0 < 0 ? 0 : d0;
+}
+
+size_t ko_fast_smem_levels_cap() { return kMaxLevels; }
+
+ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaStream_t st)
+{
+    const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * 2 * kOvCap;
+    if (fs->cap < need) {
+        cudaFree(fs->buf);
+        fs->buf = nullptr;
+        fs->cap = 0;
+        if (cudaMalloc(&fs->buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return KO_ERR_NOMEM;
+        }
+        fs->cap = need;
     }
-    fs->cap = need;
-    return KO_OK;
-}
-
-template <int LANES>
-cudaError_t launch(const FastArgs &a, cudaStream_t st)
-{
-    const int level_words = kStateWords * LANES + 4;
-    const size_t smem = sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
-    cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES>, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    const long long segs_needed = a.n_items;
-    const long long blocks_needed = (segs_needed + kThreads / LANES - 1) / (kThreads / LANES);
-    if (blocks > blocks_needed) blocks = blocks_needed;
-    if (blocks < 1) blocks = 1;
-    fast_kernel<LANES><<<(unsigned)blocks, kThreads, smem, st>>>(a);
-    ko_count_launch();
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-namespace {
-
-// Launch the fast kernel, then re-run every abandoned item with the simple
-// simulator (on the device, from the recorded list).  span = orders per item.
-ko_status run_fast(KoFastState *fs, const KoSet &h, const KoSet *d_set, FastArgs a,
-                   unsigned long long span, KoAccum *acc, cudaStream_t st)
-{
-    ko_status s = ensure_buf(fs);
-    if (s) return s;
+    if (!fs->fb_scratch) {
+        if (cudaMalloc(&fs->fb_scratch, kFallbackScratch) != cudaSuccess) {
+            cudaGetLastError();
+            return KO_ERR_NOMEM;
+        }
+        fs->fb_bytes = kFallbackScratch;
+    }
     FastBuf *fb = (FastBuf *)fs->buf;
     if (cudaMemsetAsync(fb, 0, sizeof(FastBuf), st) != cudaSuccess) return KO_ERR_CUDA;
-    a.counter = &fb->counter;
-    a.ov_count = &fb->ov_count;
-    a.ov_list = fb->ov_list;
-    a.ov_cap = kOvCap;
-    a.run_limit = fs->run_limit;
-    if (!fs->ev0 && (cudaEventCreate(&fs->ev0) != cudaSuccess || cudaEventCreate(&fs->ev1) != cudaSuccess))
-        return KO_ERR_CUDA;
-    cudaEventRecord(fs->ev0, st);
-    cudaError_t e = fs->lanes == 16 ? launch<16>(a, st) : launch<32>(a, st);
+    w.run_limit = fs->run_limit;
+    if (w.levels < 1) w.levels = 1;
+    if (w.levels > kMaxLevels) w.levels = kMaxLevels;
+    w.ov_cap = kOvCap;
+    // pass 1: all items, 8 group slots per run
+    w.counter = &fb->counter[0];
+    w.ov_count = &fb->ov_count[0];
+    w.ov_list = fb->ov_list;
+    w.item_list = nullptr;
+    w.item_count = nullptr;
+    cudaError_t e = fs->lanes == 16 ? launch<16, kG>(w, st) : launch<32, kG>(w, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_CUDA;
     }
-    cudaEventRecord(fs->ev1, st);
-    unsigned long long cnt = 0;
-    if (cudaMemcpyAsync(&cnt, &fb->ov_count, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+    // pass 2: the items pass 1 abandoned, 32 lanes and 16 group slots per run
+    KoWork w2 = w;
+    w2.counter = &fb->counter[1];
+    w2.item_list = fb->ov_list;
+    w2.item_count = &fb->ov_count[0];
+    w2.ov_count = &fb->ov_count[1];
+    w2.ov_list = fb->ov_list + kOvCap;
+    w2.run_limit = fs->run_limit;
+    e = launch<32, kGWide>(w2, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         return KO_ERR_CUDA;
-    fs->d2h += sizeof(cnt);
-    float ms = -1.0f;
-    if (cudaEventElapsedTime(&ms, fs->ev0, fs->ev1) == cudaSuccess) fs->last_ms = ms;
-    fs->last_overflow = cnt;
-    if (cnt == 0) return KO_OK;
-    if (cnt > kOvCap) return 1;  // too many abandoned items: caller redoes everything
-    s = ko_simple_items(h, d_set, a.mode == 1 ? a.idx : nullptr, fb->ov_list, (long long)cnt, span,
-                        a.out, acc, st);
-    return s;
+    }
+    // pass 3: whatever is left, simple simulator
+    KoWork w3 = w2;
+    w3.fb_counter = &fb->fb_counter;
+    e = ko_launch_fallback(w3, fs->fb_scratch, fs->fb_bytes, max_slab_bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_CUDA;
+    }
+    return KO_OK;
 }
 
-}  // namespace
-
-ko_status ko_fast_exhaustive(KoFastState *fs, const KoSet &h, const KoSet *d_set, int64_t *d_out,
-                             KoAccum *d_acc, cudaStream_t st)
+const unsigned long long *ko_fast_overflow_counter(const KoFastState *fs)
 {
-    if (fs->disabled || !applicable(h) || h.n > KO_MAX_EXHAUSTIVE) return 1;
-    FastArgs a{};
-    a.set = d_set;
-    a.mode = 0;
-    int levels = fs->levels;
-    if (levels > kMaxLevels) levels = kMaxLevels;
-    int d0 = h.n - 1 - levels;
-    if (d0 < 0) d0 = 0;
-    a.d0 = d0;
-    a.levels = h.n - 1 - d0 > 0 ? h.n - 1 - d0 : 1;
-    a.n_items = (long long)(c_fact_host(h.n) / c_fact_host(h.n - d0));
-    a.out = d_out;
-    a.acc = d_acc;
-    return run_fast(fs, h, d_set, a, c_fact_host(h.n - d0), d_acc, st);
-}
-
-ko_status ko_fast_eval_idx(KoFastState *fs, const KoSet &h, const KoSet *d_set,
-                           const uint64_t *d_idx, int64_t count, int64_t *d_out, cudaStream_t st)
-{
-    if (fs->disabled || !applicable(h) || h.n > 20) return 1;
-    FastArgs a{};
-    a.set = d_set;
-    a.mode = 1;
-    a.d0 = h.n;
-    a.levels = 1;
-    a.n_items = count;
-    a.idx = d_idx;
-    a.out = d_out;
-    a.acc = nullptr;
-    return run_fast(fs, h, d_set, a, 1, nullptr, st);
+    return fs->buf ? &((const FastBuf *)fs->buf)->ov_count[0] : nullptr;
 }
 
 void ko_fast_release(KoFastState *fs)
@@ -685,6 +701,9 @@ void ko_fast_release(KoFastState *fs)
     if (fs->ev1) cudaEventDestroy(fs->ev1);
     fs->ev0 = fs->ev1 = nullptr;
     cudaFree(fs->buf);
+    cudaFree(fs->fb_scratch);
     fs->buf = nullptr;
+    fs->fb_scratch = nullptr;
     fs->cap = 0;
+    fs->fb_bytes = 0;
 }

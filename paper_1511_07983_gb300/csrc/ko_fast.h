@@ -1,30 +1,80 @@
-// Run-length, prefix-sharing simulator (see ko_fast.cu).
+// Work lists of the run-length, prefix-sharing simulator (ko_fast.cu) and of
+// its device-side fallback (ko_sim_simple.cu).
 #pragma once
 
 #include "ko_internal.h"
 
-// Device buffers the run-length simulator keeps between calls.
-struct KoFastState {
-    void *buf = nullptr;   // work counter, abandoned-item list
-    size_t cap = 0;
-    unsigned long long last_overflow = 0;  // items the last launch handed to the simple simulator
-    int lanes = 32;                        // lanes per simulation (16 or 32)
-    int levels = 4;                        // saved DFS levels (items fix N - 1 - levels kernels)
-    bool disabled = false;                 // use the simple simulator only
-    int run_limit = 32;                    // cap on runs per simulation (tests force overflow)
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last fast-kernel launch
-    double last_ms = -1.0;
-    long long h2d = 0, d2h = 0;            // bytes copied by the fast path
+// A contiguous range of work items that belong to one set.
+struct KoChunk {
+    long long first;     // global index of the chunk's first item (chunks sorted by first)
+    long long count;     // number of items
+    int set;             // index into KoWork::sets / refs / accs
+    int d0;              // mode 0: kernels fixed by an item's prefix
+    int mode;            // 0 = exhaustive prefixes, 1 = Lehmer index list, 2 = explicit rows
+    int pad;
+    long long list_off;  // modes 1/2: entry of idx / row of perms for the chunk's first item
+    long long out_off;   // added to the output position (mode 0: Lehmer index; 1/2: item)
 };
 
-// Makespans of all N! orders into d_out (if non-null) and the accumulators.
-// Returns KO_OK, a negative ko_status, or 1 when this simulator does not apply
-// to the set (the caller then uses the simple simulator).
-ko_status ko_fast_exhaustive(KoFastState *fs, const KoSet &h, const KoSet *d_set, int64_t *d_out,
-                             KoAccum *d_acc, cudaStream_t st);
+// Parameters of one simulator launch (passed by value to the kernels).
+struct KoWork {
+    const KoSet *sets;
+    const KoChunk *chunks;
+    int nchunks;
+    long long n_items;
+    long long *refs;                  // per-set reference makespan, or null (use KoSet::ref_makespan)
+    KoAccum *accs;                    // per-set accumulators, or null
+    const uint64_t *idx;              // mode 1 entries
+    const int8_t *perms;              // mode 2 rows, n bytes each
+    int64_t *out;                     // makespans, or null
+    unsigned long long *counter;      // next work item
+    unsigned long long *ov_count;     // items abandoned by the run-length simulator
+    unsigned long long *ov_list;      // their global item indices
+    unsigned long long ov_cap;
+    unsigned long long *fb_counter;   // next abandoned item for the fallback
+    const unsigned long long *item_list;   // non-null: work items are item_list[0 .. *item_count)
+    const unsigned long long *item_count;
+    int levels;                       // saved DFS levels per segment
+    int run_limit;                    // runs one simulation may hold
+};
 
-// Makespans of `count` orders given by Lehmer index; same return convention.
-ko_status ko_fast_eval_idx(KoFastState *fs, const KoSet &h, const KoSet *d_set,
-                           const uint64_t *d_idx, int64_t count, int64_t *d_out, cudaStream_t st);
+// Device-side state of the run-length simulator, owned by a handle or batch.
+struct KoFastState {
+    void *buf = nullptr;        // counters and abandoned-item list
+    size_t cap = 0;
+    void *fb_scratch = nullptr; // fallback slabs
+    size_t fb_bytes = 0;
+    unsigned long long last_overflow = 0;
+    int lanes = 32;             // lanes per simulation (16 or 32)
+    int levels = 4;             // saved DFS levels (items fix N - 1 - levels kernels)
+    bool disabled = false;      // use the simple simulator only
+    int run_limit = 32;         // cap on runs per simulation (tests force the hand-over)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last run-length launch
+    double last_ms = -1.0;
+    long long h2d = 0, d2h = 0;
+};
+
+// True when the run-length simulator applies to the set (every possible block
+// duration below 2^31, so 32-bit modular end times are exact).
+bool ko_fast_applicable(const KoSet &h);
+
+// Prefix depth for exhaustive work items of an n-kernel set.
+int ko_fast_d0(const KoFastState &fs, int n);
+
+// Enqueue one run-length launch over `w` (counters reset here) followed by the
+// device-side fallback for abandoned items.  Fills the counter fields of w.
+// Asynchronous, graph-capturable (no host synchronisation).
+ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaStream_t st);
+
+// Device address of the count of items the first pass of the last launch
+// abandoned (followed by the count the wide second pass abandoned).
+const unsigned long long *ko_fast_overflow_counter(const KoFastState *fs);
 
 void ko_fast_release(KoFastState *fs);
+
+// Fallback: re-run the abandoned items of `w` with the simple simulator.
+cudaError_t ko_launch_fallback(const KoWork &w, void *scratch, size_t scratch_bytes,
+                               size_t per_thread, cudaStream_t st);
+
+// Bytes of one simple-simulator slab for a set.
+size_t ko_slab_bytes(int S, int Bk);

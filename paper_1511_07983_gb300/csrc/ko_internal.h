@@ -50,14 +50,6 @@ cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_
                              KoAccum *acc, void *scratch, size_t scratch_bytes,
                              cudaStream_t stream);
 
-// Simple simulator over a device list of work items: item j covers Lehmer
-// indices items[j]*span .. items[j]*span + span - 1 (writing out[index]); with
-// idx != nullptr (span 1) it covers the order idx[items[j]] (writing
-// out[items[j]]).  Allocates its own scratch.
-ko_status ko_simple_items(const KoSet &h, const KoSet *d_set, const uint64_t *idx,
-                          const unsigned long long *items, long long n_items, unsigned long long span,
-                          int64_t *out, KoAccum *acc, cudaStream_t stream);
-
 // Histogram of `count` makespans with bin = (M - min) * nbins / (max - min + 1),
 // min / max read from acc on the device; hist (device, nbins u64) is added to.
 cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum *acc,

@@ -18,6 +18,7 @@
 // Blocks of one kernel that start together on one SM share their end time and
 // are kept as one group (kernel, count, end).
 #include "ko_internal.h"
+#include "ko_fast.h"
 
 namespace {
 
@@ -274,6 +275,85 @@ simple_kernel(const KoSet *__restrict__ d_set, const int8_t *__restrict__ perms,
     }
 }
 
+__device__ __forceinline__ int find_chunk_simple(const KoChunk *chunks, int nchunks, long long item)
+{
+    int lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunks[mid].first <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Re-runs the work items the run-length simulator abandoned: one warp per
+// item, lanes split the item's orders; same outputs and accumulators.
+__global__ void __launch_bounds__(kThreads)
+fallback_kernel(KoWork w, void *scratch, size_t per_thread)
+{
+    const int lane = threadIdx.x & 31;
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long total = *w.ov_count < w.ov_cap ? *w.ov_count : w.ov_cap;
+    for (;;) {
+        unsigned long long e = 0;
+        if (lane == 0) e = atomicAdd(w.fb_counter, 1ull);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (e >= total) break;
+        const long long item = (long long)w.ov_list[e];
+        const KoChunk ch = w.chunks[find_chunk_simple(w.chunks, w.nchunks, item)];
+        const KoSet &d = w.sets[ch.set];
+        const Slab st = slab_at(scratch, per_thread, d.S, d.Bk, slot);
+        const int n = d.n;
+        const long long local = item - ch.first;
+        const long long ref = w.refs ? w.refs[ch.set] : d.ref_makespan;
+        const unsigned long long span = ch.mode == 0 ? c_fact[n - ch.d0] : 1ull;
+        unsigned long long lmin = ~0ull, lmax = 0, nb = 0, ne = 0, nw = 0;
+        for (unsigned long long o = lane; o < span; o += 32) {
+            int8_t perm[KO_MAX_KERNELS];
+            bool ok = true;
+            long long outpos;
+            if (ch.mode == 0) {
+                const unsigned long long k = (unsigned long long)local * span + o;
+                outpos = ch.out_off + (long long)k;
+                unrank(n, k, perm);
+            } else if (ch.mode == 1) {
+                const unsigned long long k = w.idx[ch.list_off + local];
+                outpos = ch.out_off + local;
+                ok = k < c_fact[n];
+                unrank(n, ok ? k : 0, perm);
+            } else {
+                outpos = ch.out_off + local;
+                uint32_t seen = 0;
+                const int8_t *row = w.perms + (ch.list_off + local) * n;
+                for (int q = 0; q < n; q++) {
+                    const int v = row[q];
+                    if (v < 0 || v >= n || ((seen >> v) & 1u)) ok = false;
+                    else seen |= 1u << v;
+                    perm[q] = (int8_t)(v < 0 || v >= n ? 0 : v);
+                }
+            }
+            const int64_t ms = ok ? simulate(d, perm, st) : -1;
+            if (w.out) w.out[outpos] = ms;
+            if (ms < 0) continue;
+            const unsigned long long u = (unsigned long long)ms;
+            lmin = u < lmin ? u : lmin;
+            lmax = u > lmax ? u : lmax;
+            nb += ms < ref; ne += ms == ref; nw += ms > ref;
+        }
+        if (w.accs) {
+            lmin = warp_min_u64(lmin); lmax = warp_max_u64(lmax);
+            nb = warp_sum_u64(nb); ne = warp_sum_u64(ne); nw = warp_sum_u64(nw);
+            if (lane == 0) {
+                KoAccum *acc = w.accs + ch.set;
+                if (lmin != ~0ull) atomicMin(&acc->min, lmin);
+                if (lmax) atomicMax(&acc->max, lmax);
+                if (nb) atomicAdd(&acc->n_better, nb);
+                if (ne) atomicAdd(&acc->n_equal, ne);
+                if (nw) atomicAdd(&acc->n_worse, nw);
+            }
+        }
+    }
+}
+
 constexpr int kHistThreads = 256;
 
 __global__ void __launch_bounds__(kHistThreads)
@@ -314,6 +394,20 @@ __global__ void accum_reset_kernel(KoAccum *acc, int count)
 
 size_t ko_simple_scratch_per_thread(const KoSet &h) { return slab_bytes(h.S, h.Bk); }
 
+size_t ko_slab_bytes(int S, int Bk) { return slab_bytes(S, Bk); }
+
+cudaError_t ko_launch_fallback(const KoWork &w, void *scratch, size_t scratch_bytes,
+                               size_t per_thread, cudaStream_t st)
+{
+    long long threads = (long long)(scratch_bytes / per_thread);
+    long long blocks = threads / kThreads;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) return cudaErrorMemoryAllocation;
+    fallback_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(w, scratch, per_thread);
+    ko_count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_t *perms,
                              const uint64_t *idx, uint64_t first, int64_t count, int64_t *out,
                              KoAccum *acc, void *scratch, size_t scratch_bytes, cudaStream_t stream)
@@ -332,32 +426,6 @@ cudaError_t ko_launch_simple(const KoSet *d_set, const KoSet &h_set, const int8_
     return cudaGetLastError();
 }
 
-ko_status ko_simple_items(const KoSet &h, const KoSet *d_set, const uint64_t *idx,
-                          const unsigned long long *items, long long n_items, unsigned long long span,
-                          int64_t *out, KoAccum *acc, cudaStream_t stream)
-{
-    const long long count = n_items * (long long)span;
-    if (count <= 0) return KO_OK;
-    const size_t per = slab_bytes(h.S, h.Bk);
-    long long slots = (long long)((size_t(256) << 20) / per);
-    long long blocks = slots / kThreads;
-    const long long need = (count + kThreads - 1) / kThreads;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    if (blocks > 65535) blocks = 65535;
-    void *scratch = nullptr;
-    if (cudaMalloc(&scratch, per * (size_t)blocks * kThreads) != cudaSuccess) {
-        cudaGetLastError();
-        return KO_ERR_NOMEM;
-    }
-    simple_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(d_set, nullptr, idx, items, span, 0,
-                                                             count, out, acc, scratch, per);
-    ko_count_launch();
-    cudaError_t e = cudaGetLastError();
-    cudaError_t e2 = cudaStreamSynchronize(stream);
-    cudaFree(scratch);
-    return (e == cudaSuccess && e2 == cudaSuccess) ? KO_OK : KO_ERR_CUDA;
-}
 
 cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum *acc,
                                 unsigned long long *hist, int32_t nbins, cudaStream_t stream)
