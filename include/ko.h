@@ -167,6 +167,18 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 #define KO_OPT_RUN_LIMIT 4
 ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 
+/* Current value of a tuning knob (KO_OPT_*), or KO_ERR_ARG. */
+int64_t ko_get_option(const ko_gpu *g, int32_t key);
+
+/* Autotuner: times the run-length simulator on a calibration slice of this
+ * set's exhaustive space for every candidate (16 or 32 lanes per simulation;
+ * 1..min(N-1, 6) saved DFS levels, skipping depths that leave too few work
+ * items), keeps the fastest and sets KO_OPT_LANES / KO_OPT_LEVELS on the
+ * handle.  With cache_path (nullable) the choice is looked up first and
+ * stored after, keyed by (N_SM class, N), in a small JSON file.  Synchronises
+ * `stream`; results never depend on the choice.  N <= 12. */
+ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream);
+
 /* Work items the last exhaustive or index-list call moved from the
  * run-length simulator to the simple one (a simulation needed more runs of
  * distinct SM states than lanes, or more than 8 resident groups in a run);
@@ -185,6 +197,38 @@ double ko_last_sim_ms(const ko_gpu *g);
 /* Bytes this handle has copied host->device and device->host since it was
  * created (inputs, staged buffers, results).  KO_ERR_ARG on NULL arguments. */
 ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent sets scored in one persistent launch (the exhaustive
+ * evaluation of Sec. 6 repeated over a population of kernel sets).
+ *
+ * ko_batch_create snapshots nsets handles (kernels, limits, capacities and
+ * each handle's KO_OPT_LEVELS; KO_OPT_LANES and KO_OPT_RUN_LIMIT of the
+ * first handle), computes
+ * each set's Algorithm 1 order on the host, lays out one work list over all
+ * sets (largest sets first) and captures the whole evaluation -- reset,
+ * ranked-order makespans, all N! orders of every set, optional per-set
+ * histograms, copy-out -- as one CUDA graph.  Every set needs 1 <= N <= 12
+ * (KO_ERR_TOO_LARGE above) and durations below 2^31 cycles (KO_ERR_OVERFLOW).
+ * nbins = 0 skips histograms (and the per-set makespan storage, 8 bytes per
+ * order); 1..32768 keeps them.  Returns NULL on error (ko_last_error()).
+ * The batch owns its device memory; the handles may be destroyed afterwards. */
+typedef struct ko_batch ko_batch;
+ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins);
+
+/* Launch the captured graph on `stream` and wait for it.  out[i] (host,
+ * nsets entries) receives set i's statistics and the rank of its Algorithm 1
+ * order (ko_rank fields as in ko_rank_order).  hist (host or device,
+ * nsets x nbins, row i = set i) may be NULL. */
+ko_status ko_batch_run(ko_batch *b, ko_rank *out, uint64_t *hist, void *stream);
+
+/* Total number of orders one ko_batch_run evaluates (sum of N_i!), or -1. */
+int64_t ko_batch_orders(const ko_batch *b);
+
+/* Work items of the last run that moved to the wide pass (diagnostic), or -1. */
+int64_t ko_batch_fallback_items(const ko_batch *b);
+
+void ko_batch_destroy(ko_batch *b);
 
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);

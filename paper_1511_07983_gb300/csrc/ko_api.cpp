@@ -561,6 +561,38 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
     return ok();
 }
 
+int64_t ko_get_option(const ko_gpu *g, int32_t key)
+{
+    if (!g) return fail(KO_ERR_ARG);
+    switch (key) {
+    case KO_OPT_LANES: return g->fast.lanes;
+    case KO_OPT_LEVELS: return g->fast.levels;
+    case KO_OPT_SIMPLE_ONLY: return g->fast.disabled ? 1 : 0;
+    case KO_OPT_RUN_LIMIT: return g->fast.run_limit;
+    default: return fail(KO_ERR_ARG);
+    }
+}
+
+ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream)
+{
+    if (!g || g->h.n < 1) return fail(KO_ERR_ARG);
+    if (g->h.n > KO_MAX_EXHAUSTIVE) return fail(KO_ERR_TOO_LARGE);
+    if (!ko_fast_applicable(g->h)) return ok();  // only the simple simulator applies
+    cudaStream_t st = (cudaStream_t)stream;
+    g->h.ref_makespan = 0;
+    ko_status s = prepare(g, st);
+    if (s) return fail(s);
+    if ((s = upload_meta(g, st))) return fail(s);
+    int lanes = 32, levels = 4;
+    double rate = 0.0;
+    s = ko_tune_set(&g->fast, g->h, g->d_set, &g->d_meta->chunk[1], g->d_acc, cache_path, st, &lanes,
+                    &levels, &rate);
+    if (s) return fail(s);
+    g->fast.lanes = lanes;
+    g->fast.levels = levels;
+    return ok();
+}
+
 int64_t ko_last_fallback_items(const ko_gpu *g)
 {
     if (!g) return -1;
@@ -572,6 +604,44 @@ int64_t ko_last_fallback_items(const ko_gpu *g)
     }
     return (int64_t)g->fast.last_overflow;
 }
+
+ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
+{
+    if (!sets || nsets < 1) {
+        fail(KO_ERR_ARG);
+        return nullptr;
+    }
+    std::vector<const KoSet *> hs(nsets);
+    std::vector<int> levels(nsets);
+    for (int i = 0; i < nsets; i++) {
+        if (!sets[i]) {
+            fail(KO_ERR_ARG);
+            return nullptr;
+        }
+        sets[i]->frozen = true;
+        hs[i] = &sets[i]->h;
+        levels[i] = sets[i]->fast.levels;
+    }
+    ko_status err = KO_OK;
+    ko_batch *b = ko_batch_build(hs.data(), levels.data(), nsets, nbins, sets[0]->fast.lanes,
+                                 sets[0]->fast.run_limit, &err);
+    if (!b) fail(err);
+    else ok();
+    return b;
+}
+
+ko_status ko_batch_run(ko_batch *b, ko_rank *out, uint64_t *hist, void *stream)
+{
+    if (!b || !out) return fail(KO_ERR_ARG);
+    ko_status s = ko_batch_exec(b, out, hist, is_device_ptr(hist), (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+int64_t ko_batch_orders(const ko_batch *b) { return b ? (int64_t)ko_batch_orders_impl(b) : -1; }
+
+int64_t ko_batch_fallback_items(const ko_batch *b) { return b ? (int64_t)ko_batch_fallback(b) : -1; }
+
+void ko_batch_destroy(ko_batch *b) { ko_batch_free(b); }
 
 void ko_destroy_gpu(ko_gpu *g) { delete g; }
 

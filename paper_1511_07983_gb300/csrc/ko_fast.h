@@ -12,7 +12,7 @@ struct KoChunk {
     int d0;              // mode 0: kernels fixed by an item's prefix
     int mode;            // 0 = exhaustive prefixes, 1 = Lehmer index list, 2 = explicit rows
     int pad;
-    long long list_off;  // modes 1/2: entry of idx / row of perms for the chunk's first item
+    long long list_off;  // mode 1: entry of idx for the first item; mode 2: byte offset of its row
     long long out_off;   // added to the output position (mode 0: Lehmer index; 1/2: item)
 };
 

@@ -58,6 +58,21 @@ cudaError_t ko_launch_histogram(const int64_t *ms, int64_t count, const KoAccum 
 // Resets an accumulator to (min = max u64, max = 0, counts = 0).
 cudaError_t ko_launch_accum_reset(KoAccum *acc, int count, cudaStream_t stream);
 
+// Batch internals (ko_batch.cpp).
+ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets, int nbins, int lanes,
+                         int run_limit, ko_status *err);
+ko_status ko_batch_exec(ko_batch *b, ko_rank *out, uint64_t *hist, bool hist_dev, cudaStream_t st);
+long long ko_batch_orders_impl(const ko_batch *b);
+unsigned long long ko_batch_fallback(const ko_batch *b);
+void ko_batch_free(ko_batch *b);
+
+// Autotuner internals (ko_tune.cpp).
+struct KoFastState;
+struct KoChunk;
+ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
+                      KoAccum *d_acc, const char *cache_path, cudaStream_t st, int *lanes_out,
+                      int *levels_out, double *rate_out);
+
 // Host-side Algorithm 1; returns the number of execution rounds.
 int ko_heuristic_host(const KoSet &h, int32_t *order_out);
 

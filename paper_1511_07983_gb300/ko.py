@@ -57,10 +57,18 @@ _SIGNATURES = {
     "ko_eval_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ko_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_last_fallback_items": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ko_get_option": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int32]),
+    "ko_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]),
     "ko_kernel_launches": (ctypes.c_int64, []),
     "ko_last_sim_ms": (ctypes.c_double, [ctypes.c_void_p]),
     "ko_transfer_bytes": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
+    "ko_batch_create": (ctypes.c_void_p, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32]),
+    "ko_batch_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ko_rank), ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "ko_batch_orders": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ko_batch_fallback_items": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ko_batch_destroy": (None, [ctypes.c_void_p]),
     "ko_destroy_gpu": (None, [ctypes.c_void_p]),
     "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "ko_last_error": (ctypes.c_int32, []),
@@ -187,6 +195,15 @@ def ko_set_option(g, key, value):
     return _check(lib().ko_set_option(g, key, value), "ko_set_option")
 
 
+def ko_get_option(g, key):
+    return _check(lib().ko_get_option(g, key), "ko_get_option")
+
+
+def ko_autotune(g, cache_path=None, stream=None):
+    p = cache_path.encode() if cache_path else None
+    return _check(lib().ko_autotune(g, p, _stream(stream)), "ko_autotune")
+
+
 def ko_last_fallback_items(g):
     return lib().ko_last_fallback_items(g)
 
@@ -215,6 +232,63 @@ def ko_status_str(code):
 
 def ko_last_error():
     return lib().ko_last_error()
+
+
+def ko_batch_create(handles, nbins=0):
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    b = lib().ko_batch_create(arr, len(handles), nbins)
+    if not b:
+        raise KoError(lib().ko_last_error(), "ko_batch_create")
+    return b
+
+
+def ko_batch_run(b, nsets, hist=None, stream=None):
+    out = (ko_rank * nsets)()
+    _check(lib().ko_batch_run(b, out, _ptr(hist), _stream(stream)), "ko_batch_run")
+    return [r.as_dict() for r in out]
+
+
+def ko_batch_orders(b):
+    return lib().ko_batch_orders(b)
+
+
+def ko_batch_fallback_items(b):
+    return lib().ko_batch_fallback_items(b)
+
+
+def ko_batch_destroy(b):
+    lib().ko_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper of a ko_batch (many sets, one captured graph)."""
+
+    def __init__(self, gpus, nbins=0):
+        self.nsets = len(gpus)
+        self.nbins = nbins
+        self.b = ko_batch_create([g.h for g in gpus], nbins)
+
+    def run(self, hist=None, stream=None):
+        if hist is None and self.nbins:
+            hist = np.zeros((self.nsets, self.nbins), dtype=np.uint64)
+        return ko_batch_run(self.b, self.nsets, hist=hist, stream=stream), hist
+
+    def orders(self):
+        return ko_batch_orders(self.b)
+
+    def fallback_items(self):
+        return ko_batch_fallback_items(self.b)
+
+    def close(self):
+        if self.b:
+            ko_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------ convenience
@@ -273,6 +347,11 @@ class Gpu:
 
     def last_fallback_items(self):
         return ko_last_fallback_items(self.h)
+
+    def autotune(self, cache_path=None, stream=None):
+        ko_autotune(self.h, cache_path, stream)
+        return {"lanes": ko_get_option(self.h, KO_OPT_LANES),
+                "levels": ko_get_option(self.h, KO_OPT_LEVELS)}
 
     def last_sim_ms(self):
         return ko_last_sim_ms(self.h)

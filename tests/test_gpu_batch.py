@@ -1,0 +1,79 @@
+"""GPU parity of the batched launch: per-set statistics and histograms of many
+sets in one captured graph equal the oracle's, and equal one-set calls."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_07983_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ko():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1511_07983_gb300 import build, ko as kmod
+    build.build()
+    torch.cuda.init()
+    return kmod
+
+
+def _oracle_stats(s, nbins):
+    h = oracle.heuristic(s.gpu, s.kernels)
+    mh = oracle.makespan(s.gpu, s.kernels, h)
+    return oracle.exhaustive_stats(s.gpu, s.kernels, mh, nbins=nbins)
+
+
+def test_batch_small_sets_match_oracle(ko):
+    # uneven N, mixed simulated GPUs; every set small enough for the oracle
+    sets = []
+    for i in range(60):
+        s = synth.gen_set("batched", i)
+        if s.n <= 7:
+            sets.append(s)
+    sets = sets[:24]
+    gpus = [ko.Gpu.from_set(s) for s in sets]
+    b = ko.Batch(gpus, nbins=256)
+    for rep in range(2):   # the graph replays with identical results
+        res, hist = b.run()
+        for s, r, h in zip(sets, res, hist):
+            st = _oracle_stats(s, 256)
+            assert (r["min"], r["max"], r["makespan"], r["n_total"]) == \
+                (st["min"], st["max"], st["makespan"], st["n_total"])
+            assert (r["n_better"], r["n_equal"], r["n_worse"]) == \
+                (st["n_better"], st["n_equal"], st["n_worse"])
+            assert np.array_equal(h, st["hist"])
+    assert b.orders() == sum(math.factorial(s.n) for s in sets)
+
+
+def test_batch_equals_single_set_calls(ko):
+    sets = [synth.gen_set("batched", i) for i in range(30, 46)]
+    gpus = [ko.Gpu.from_set(s) for s in sets]
+    b = ko.Batch(gpus, nbins=0)
+    res, _ = b.run()
+    for s, r in zip(sets, res):
+        with ko.Gpu.from_set(s) as g:
+            one, _ = g.rank_order(None, nbins=0)
+        for k in ("min", "max", "makespan", "n_better", "n_equal", "n_worse", "n_total"):
+            assert r[k] == one[k], k
+
+
+def test_batch_forced_handover(ko):
+    sets = [synth.gen_set("batched", i) for i in range(60) if synth.gen_set("batched", i).n <= 6][:6]
+    gpus = [ko.Gpu.from_set(s).configure(run_limit=2) for s in sets]
+    b = ko.Batch(gpus, nbins=64)
+    res, hist = b.run()
+    for s, r, h in zip(sets, res, hist):
+        st = _oracle_stats(s, 64)
+        assert (r["min"], r["max"], r["n_equal"]) == (st["min"], st["max"], st["n_equal"])
+        assert np.array_equal(h, st["hist"])
+
+
+def test_batch_rejects_large_sets(ko):
+    s = synth.random_set(1, 13)
+    with pytest.raises(ko.KoError) as e:
+        ko.Batch([ko.Gpu.from_set(s)])
+    assert e.value.code == -3
