@@ -56,7 +56,20 @@ struct SetConst {
     int total_blocks;
     int r[KO_MAX_KERNELS], s[KO_MAX_KERNELS], w[KO_MAX_KERNELS], b[KO_MAX_KERNELS];
     int c[KO_MAX_KERNELS], m[KO_MAX_KERNELS];
+    float rr[KO_MAX_KERNELS], rs[KO_MAX_KERNELS], rw[KO_MAX_KERNELS];  // 1/r, 1/s, 1/w
 };
+
+// floor(x / d) for 0 <= x <= 2^24 and d >= 1, clamped to at most 32: the
+// quotient of min(x, 32 d) estimated with a float reciprocal (error far below
+// one unit at that size) and corrected once by an exact integer check.
+__device__ __forceinline__ int quot32(int x, int d, float rcp)
+{
+    const int xc = min(x, d << 5);
+    int q = __float2int_rz(__int2float_rn(xc) * rcp);
+    if ((q + 1) * d <= xc) q++;
+    if (q * d > xc) q--;
+    return q;
+}
 
 template <int LANES>
 struct Seg {
@@ -163,9 +176,9 @@ struct Sim {
         int cap = 0;
         if (run.cnt > 0) {
             cap = K.Bk - run.ub;
-            cap = min(cap, (K.R - run.ur) / r);
-            cap = min(cap, (K.W - run.uw) / w);
-            if (s > 0) cap = min(cap, (K.Sh - run.us) / s);
+            cap = min(cap, quot32(K.R - run.ur, r, K.rr[kid]));
+            cap = min(cap, quot32(K.W - run.uw, w, K.rw[kid]));
+            if (s > 0) cap = min(cap, quot32(K.Sh - run.us, s, K.rs[kid]));
             cap = max(cap, 0);
         }
         const int total = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * cap));
@@ -368,6 +381,9 @@ __device__ void load_set(SetConst &K, const KoSet *d, const Seg<LANES> &sg)
     for (int i = sg.lane; i < KO_MAX_KERNELS; i += LANES) {
         const KoKern kk = d->k[i];
         K.r[i] = kk.r; K.s[i] = kk.s; K.w[i] = kk.w; K.b[i] = kk.b; K.c[i] = kk.c; K.m[i] = kk.m;
+        K.rr[i] = kk.r > 0 ? 1.0f / (float)kk.r : 0.0f;
+        K.rs[i] = kk.s > 0 ? 1.0f / (float)kk.s : 0.0f;
+        K.rw[i] = kk.w > 0 ? 1.0f / (float)kk.w : 0.0f;
         if (i < d->n) nb += kk.b;
     }
     nb = (int)__reduce_add_sync(sg.mask, (unsigned)nb);

@@ -111,3 +111,18 @@ def test_batched_sets_exhaustive_small(ko, workload, count):
             assert np.array_equal(_all(g, s.n), want), i
         checked += 1
     assert checked > 5
+
+
+def test_autotune_choice_cache_and_exactness(ko, tmp_path):
+    import json
+    s = synth.gen_set("sets10", 7, n=8)
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=40320)
+    cache = str(tmp_path / "tune.json")
+    with ko.Gpu.from_set(s) as g:
+        choice = g.autotune(cache)
+        assert choice["lanes"] in (16, 32) and 1 <= choice["levels"] <= 6
+        assert np.array_equal(_all(g, 8), want)
+    data = json.load(open(cache))
+    assert data["S16_N8"]["lanes"] == choice["lanes"] and data["S16_N8"]["levels"] == choice["levels"]
+    with ko.Gpu.from_set(s) as g:   # second handle: served from the cache
+        assert g.autotune(cache) == choice
