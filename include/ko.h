@@ -230,6 +230,69 @@ int64_t ko_batch_fallback_items(const ko_batch *b);
 
 void ko_batch_destroy(ko_batch *b);
 
+/* -------------------------------------------------------------- surrogate
+ * Not part of the paper.  For sets too large to enumerate (N = 16..24), a
+ * small MLP predicts log2(makespan / lower bound) of an order from
+ * position-ordered kernel descriptors; it is trained on orders the exact
+ * simulator labels, proposes the best-predicted of many random candidates,
+ * and every proposal is rescored exactly, so the simulator stays the judge.
+ *
+ * Network: 192 inputs -> 256 -> 256 -> 256 -> 1, ReLU, BF16 weights and
+ * activations, FP32 accumulation on tensor cores; MSE loss; Adam
+ * (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights.
+ * Inputs: 24 position slots x 7 features (regs/N_reg_SM, smem/N_shm_SM,
+ * warps/N_warp_SM, ceil(N_tblk/N_SM)/N_blk_SM, log2(c)/16, log2(m)/16,
+ * present) + 8 globals (N/24, N_SM/148, log2 of the four limits / 24,
+ * log2(lower bound)/32, 1) + 16 zeros; the kernel at position p of an N-kernel
+ * order goes to slot round(23 p / (N-1)).
+ * Parameters (KO_MODEL_PARAMS floats, host order): W1 [192 x 256] (input-
+ * major), b1 [256], W2 [256 x 256], b2, W3 [256 x 256], b3, w4 [256], b4. */
+#define KO_MODEL_PARAMS 181249
+typedef struct ko_model ko_model;
+
+/* He-normal initial weights from a counter-based SplitMix64 stream. */
+ko_model *ko_model_create(uint64_t seed);
+ko_status ko_model_get_params(const ko_model *m, float *params);   /* host out */
+ko_status ko_model_set_params(ko_model *m, const float *params);   /* host in; resets Adam */
+
+/* Raw-feature entry points (B % 64 == 0, B >= 64; x host [B x 192], values
+ * rounded to BF16 on upload; t host [B]).  ko_model_predict writes y [B];
+ * ko_model_grad also writes the FP32 gradient of the mean squared error
+ * (KO_MODEL_PARAMS floats, host) and the loss; ko_model_train_step does the
+ * same and then one Adam step with learning rate lr. */
+ko_status ko_model_predict(ko_model *m, const float *x, int64_t B, float *y, void *stream);
+ko_status ko_model_grad(ko_model *m, const float *x, const float *t, int64_t B, float *grad,
+                        float *loss, void *stream);
+ko_status ko_model_train_step(ko_model *m, const float *x, const float *t, int64_t B, float lr,
+                              float *loss, void *stream);
+
+/* Encoder output for n explicit orders (host, n x N ids) of a set: host
+ * x_out [n x 192] (BF16 values as floats). */
+ko_status ko_model_encode(ko_gpu *g, const int8_t *orders, int64_t n, float *x_out, void *stream);
+
+/* Train on simulator-labelled pairs: for each of nsets sets, pairs_per_set
+ * uniform random orders (device RNG from `seed`) labelled exactly; then
+ * `steps` Adam steps on random minibatches of `batch` (multiple of 64) pairs.
+ * loss_curve (host, nullable) receives the mean loss of every step. */
+ko_status ko_surrogate_train(ko_model *m, ko_gpu *const *sets, int32_t nsets, int64_t pairs_per_set,
+                             int32_t steps, int32_t batch, float lr, uint64_t seed,
+                             float *loss_curve, void *stream);
+
+/* Propose an order for a set of any N <= 24: draw n_cand uniform random
+ * candidates, score them with the network, keep the top_k best predicted,
+ * rescore those exactly and return the best (best_order: host, N ids).
+ * gpu_ms (nullable) receives the device time of the whole proposal. */
+ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, uint64_t seed,
+                               int32_t *best_order, int64_t *best_makespan, double *gpu_ms,
+                               void *stream);
+
+/* Plain random search, the baseline of the surrogate: n_orders uniform random
+ * orders simulated exactly; the best one is returned. */
+ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
+                           int64_t *best_makespan, double *gpu_ms, void *stream);
+
+void ko_model_destroy(ko_model *m);
+
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);
 

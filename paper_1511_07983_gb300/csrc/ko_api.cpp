@@ -643,6 +643,99 @@ int64_t ko_batch_fallback_items(const ko_batch *b) { return b ? (int64_t)ko_batc
 
 void ko_batch_destroy(ko_batch *b) { ko_batch_free(b); }
 
+ko_model *ko_model_create(uint64_t seed)
+{
+    ko_status err = KO_OK;
+    ko_model *m = ko_model_new(seed, &err);
+    if (!m) fail(err);
+    else ok();
+    return m;
+}
+
+ko_status ko_model_get_params(const ko_model *m, float *params)
+{
+    if (!m || !params) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_store(m, params);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_set_params(ko_model *m, const float *params)
+{
+    if (!m || !params) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_load(m, params);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_predict(ko_model *m, const float *x, int64_t B, float *y, void *stream)
+{
+    if (!m || !x || !y || B < 64 || B % 64 || B > (1 << 24)) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_raw(m, x, nullptr, (int)B, y, nullptr, nullptr, 0.0f, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_grad(ko_model *m, const float *x, const float *t, int64_t B, float *grad, float *loss,
+                        void *stream)
+{
+    if (!m || !x || !t || !grad || B < 64 || B % 64 || B > (1 << 24)) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_raw(m, x, t, (int)B, nullptr, grad, loss, 0.0f, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_train_step(ko_model *m, const float *x, const float *t, int64_t B, float lr, float *loss,
+                              void *stream)
+{
+    if (!m || !x || !t || B < 64 || B % 64 || B > (1 << 24) || !(lr > 0.0f)) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_raw(m, x, t, (int)B, nullptr, nullptr, loss, lr, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_encode(ko_gpu *g, const int8_t *orders, int64_t n, float *x_out, void *stream)
+{
+    if (!g || !orders || !x_out || n < 1 || g->h.n < 1) return fail(KO_ERR_ARG);
+    for (int64_t i = 0; i < n * g->h.n; i++)
+        if (orders[i] < 0 || orders[i] >= g->h.n) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_features(g->h, orders, n, x_out, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_surrogate_train(ko_model *m, ko_gpu *const *sets, int32_t nsets, int64_t pairs_per_set,
+                             int32_t steps, int32_t batch, float lr, uint64_t seed, float *loss_curve,
+                             void *stream)
+{
+    if (!m || !sets || nsets < 1) return fail(KO_ERR_ARG);
+    std::vector<const KoSet *> hs(nsets);
+    for (int i = 0; i < nsets; i++) {
+        if (!sets[i] || sets[i]->h.n < 1) return fail(KO_ERR_ARG);
+        sets[i]->frozen = true;
+        hs[i] = &sets[i]->h;
+    }
+    ko_status s = ko_model_train_sets(m, hs.data(), nsets, pairs_per_set, steps, batch, lr, seed, loss_curve,
+                                      (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, uint64_t seed,
+                               int32_t *best_order, int64_t *best_makespan, double *gpu_ms, void *stream)
+{
+    if (!m || !g || !best_order || !best_makespan || g->h.n < 1) return fail(KO_ERR_ARG);
+    g->frozen = true;
+    ko_status s = ko_model_propose_set(m, g->h, n_cand, top_k, seed, best_order, best_makespan, gpu_ms,
+                                       (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
+                           int64_t *best_makespan, double *gpu_ms, void *stream)
+{
+    if (!g || !best_order || !best_makespan || g->h.n < 1) return fail(KO_ERR_ARG);
+    g->frozen = true;
+    ko_status s = ko_random_search_set(&g->fast, g->h, n_orders, seed, best_order, best_makespan, gpu_ms,
+                                       (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+void ko_model_destroy(ko_model *m) { ko_model_free(m); }
+
 void ko_destroy_gpu(ko_gpu *g) { delete g; }
 
 const char *ko_status_str(ko_status s)

@@ -497,7 +497,7 @@ fast_kernel(KoWork a)
         } else if (ch.mode == 2) {
             d0 = n;
             outpos = ch.out_off + local;
-            const int8_t *row = a.perms + ch.list_off + local * n;
+            const int8_t *row = a.perms + ch.list_off + local * (a.perm_stride ? a.perm_stride : n);
             for (int j = 0; j < n; j++) {
                 const int v = row[j];
                 if (v < 0 || v >= n || ((used >> v) & 1u)) { valid = false; break; }

@@ -25,7 +25,8 @@ struct KoWork {
     long long *refs;                  // per-set reference makespan, or null (use KoSet::ref_makespan)
     KoAccum *accs;                    // per-set accumulators, or null
     const uint64_t *idx;              // mode 1 entries
-    const int8_t *perms;              // mode 2 rows, n bytes each
+    const int8_t *perms;              // mode 2 rows
+    int perm_stride;                  // bytes between mode-2 rows (0: N of the row's set)
     int64_t *out;                     // makespans, or null
     unsigned long long *counter;      // next work item
     unsigned long long *ov_count;     // items abandoned by the run-length simulator

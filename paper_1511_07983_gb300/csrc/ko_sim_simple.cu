@@ -323,7 +323,7 @@ fallback_kernel(KoWork w, void *scratch, size_t per_thread)
             } else {
                 outpos = ch.out_off + local;
                 uint32_t seen = 0;
-                const int8_t *row = w.perms + ch.list_off + local * n;
+                const int8_t *row = w.perms + ch.list_off + local * (w.perm_stride ? w.perm_stride : n);
                 for (int q = 0; q < n; q++) {
                     const int v = row[q];
                     if (v < 0 || v >= n || ((seen >> v) & 1u)) ok = false;

@@ -69,6 +69,27 @@ _SIGNATURES = {
     "ko_batch_orders": (ctypes.c_int64, [ctypes.c_void_p]),
     "ko_batch_fallback_items": (ctypes.c_int64, [ctypes.c_void_p]),
     "ko_batch_destroy": (None, [ctypes.c_void_p]),
+    "ko_model_create": (ctypes.c_void_p, [ctypes.c_uint64]),
+    "ko_model_get_params": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_model_set_params": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_model_predict": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "ko_model_grad": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+    "ko_model_train_step": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+    "ko_model_encode": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "ko_surrogate_train": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "ko_surrogate_propose": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "ko_random_search": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]),
+    "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_destroy_gpu": (None, [ctypes.c_void_p]),
     "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "ko_last_error": (ctypes.c_int32, []),
@@ -289,6 +310,93 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+KO_MODEL_PARAMS = 181249
+
+
+class Model:
+    """Owning wrapper of a ko_model (surrogate MLP)."""
+
+    def __init__(self, seed=0):
+        self.m = lib().ko_model_create(seed)
+        if not self.m:
+            raise KoError(lib().ko_last_error(), "ko_model_create")
+
+    def get_params(self):
+        out = np.empty(KO_MODEL_PARAMS, dtype=np.float32)
+        _check(lib().ko_model_get_params(self.m, _ptr(out)), "ko_model_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        assert flat.size == KO_MODEL_PARAMS
+        _check(lib().ko_model_set_params(self.m, _ptr(flat)), "ko_model_set_params")
+
+    def predict(self, x, stream=None):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+        y = np.empty(x.shape[0], dtype=np.float32)
+        _check(lib().ko_model_predict(self.m, _ptr(x), x.shape[0], _ptr(y), _stream(stream)), "ko_model_predict")
+        return y
+
+    def grad(self, x, t, stream=None):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        g = np.empty(KO_MODEL_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().ko_model_grad(self.m, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss),
+                                   _stream(stream)), "ko_model_grad")
+        return g, loss.value
+
+    def train_step(self, x, t, lr, stream=None):
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        loss = ctypes.c_float()
+        _check(lib().ko_model_train_step(self.m, _ptr(x), _ptr(t), x.shape[0], lr, ctypes.byref(loss),
+                                         _stream(stream)), "ko_model_train_step")
+        return loss.value
+
+    def train(self, gpus, pairs_per_set, steps, batch=8192, lr=1e-3, seed=0, stream=None):
+        arr = (ctypes.c_void_p * len(gpus))(*[g.h for g in gpus])
+        curve = np.zeros(steps, dtype=np.float32)
+        _check(lib().ko_surrogate_train(self.m, arr, len(gpus), pairs_per_set, steps, batch, lr, seed,
+                                        _ptr(curve), _stream(stream)), "ko_surrogate_train")
+        return curve
+
+    def propose(self, g, n_cand, top_k=1024, seed=0, stream=None):
+        order = np.zeros(max(g.n, 1), dtype=np.int32)
+        ms = ctypes.c_int64()
+        t = ctypes.c_double()
+        _check(lib().ko_surrogate_propose(self.m, g.h, n_cand, top_k, seed, _ptr(order), ctypes.byref(ms),
+                                          ctypes.byref(t), _stream(stream)), "ko_surrogate_propose")
+        return order[:g.n], ms.value, t.value
+
+    def close(self):
+        if self.m:
+            lib().ko_model_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ko_model_encode(g, orders, stream=None):
+    orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int8))
+    x = np.empty((orders.shape[0], 192), dtype=np.float32)
+    _check(lib().ko_model_encode(g.h, _ptr(orders), orders.shape[0], _ptr(x), _stream(stream)), "ko_model_encode")
+    return x
+
+
+def ko_random_search(g, n_orders, seed=0, stream=None):
+    order = np.zeros(max(g.n, 1), dtype=np.int32)
+    ms = ctypes.c_int64()
+    t = ctypes.c_double()
+    _check(lib().ko_random_search(g.h, n_orders, seed, _ptr(order), ctypes.byref(ms), ctypes.byref(t),
+                                  _stream(stream)), "ko_random_search")
+    return order[:g.n], ms.value, t.value
 
 
 # ------------------------------------------------------------ convenience

@@ -1,0 +1,131 @@
+"""GPU checks of the surrogate: encoder equal to the oracle's, forward and
+gradients within BF16 tolerances of the oracle (FP64 accumulation, same
+rounding points), Adam, training, and proposals confirmed by the exact oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1511_07983_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ko():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1511_07983_gb300 import build, ko as kmod
+    build.build()
+    torch.cuda.init()
+    return kmod
+
+
+def _flat(p):
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"],
+                           p["w4"], p["b4"]]).astype(np.float32)
+
+
+def _split(flat):
+    out, off = {}, 0
+    for k, shape in (("W1", (192, 256)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+                     ("W3", (256, 256)), ("b3", (256,)), ("w4", (256,)), ("b4", (1,))):
+        n = int(np.prod(shape))
+        out[k] = flat[off:off + n].reshape(shape)
+        off += n
+    return out
+
+
+def _params(seed):
+    p = mlp.init_params(seed)
+    rng = np.random.default_rng(seed + 10)
+    for k in ("b1", "b2", "b3"):
+        p[k] = (rng.standard_normal(256) * 0.05).astype(np.float32)
+    p["b4"] = np.array([0.2], dtype=np.float32)
+    return p
+
+
+def _features(seed, B):
+    s = synth.gen_set("large", seed)
+    lb, _ = oracle.bounds(s.gpu, s.kernels)
+    x = mlp.encode(mlp.kernel_features(s.gpu, s.kernels), mlp.global_features(s.gpu, s.n, lb),
+                   synth.random_orders(seed, s.n, B))
+    return mlp.bf16(x)
+
+
+def test_encoder_matches_oracle(ko):
+    for i in range(6):
+        s = synth.gen_set("large" if i % 2 else "train", i)
+        orders = synth.random_orders(i, s.n, 50)
+        lb, _ = oracle.bounds(s.gpu, s.kernels)
+        want = mlp.bf16(mlp.encode(mlp.kernel_features(s.gpu, s.kernels),
+                                   mlp.global_features(s.gpu, s.n, lb), orders))
+        with ko.Gpu.from_set(s) as g:
+            got = ko.ko_model_encode(g, orders)
+        assert np.array_equal(got, want), i
+
+
+def test_forward_matches_oracle(ko):
+    p = _params(1)
+    x = _features(2, 512)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    y = m.predict(x)
+    want, _ = mlp.forward(p, x)
+    err = np.abs(y - want)
+    assert err.max() <= 2e-2 * max(1.0, np.abs(want).max()), err.max()
+    assert np.quantile(err, 0.99) <= 1e-2 * max(1.0, np.abs(want).max())
+
+
+def test_gradients_match_oracle(ko):
+    p = _params(3)
+    x = _features(4, 256)
+    t = np.random.default_rng(5).standard_normal(256).astype(np.float32)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    g, loss = m.grad(x, t)
+    y, cache = mlp.forward(p, x)
+    want = mlp.backward(p, cache, y, t)
+    assert loss == pytest.approx(mlp.loss(y, t), rel=1e-2)
+    got = _split(g)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
+        rel = np.linalg.norm(got[k] - want[k]) / max(np.linalg.norm(want[k]), 1e-12)
+        assert rel <= 2e-2, (k, rel)
+
+
+def test_adam_step_matches_oracle_update(ko):
+    p = _params(6)
+    x = _features(7, 128)
+    t = np.random.default_rng(8).standard_normal(128).astype(np.float32)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    g, _ = m.grad(x, t)
+    m.train_step(x, t, lr=1e-3)
+    after = _split(m.get_params())
+    q = {k: v.copy() for k, v in p.items()}
+    mlp.adam(q, _split(g.astype(np.float64)), {}, step=1, lr=1e-3)
+    for k in q:
+        assert np.allclose(after[k], q[k], atol=1e-6, rtol=1e-5), k
+
+
+def test_training_lowers_loss_and_ranks_orders(ko):
+    train_sets = [synth.gen_set("train", i) for i in range(24)]
+    gpus = [ko.Gpu.from_set(s) for s in train_sets]
+    m = ko.Model(seed=3)
+    curve = m.train(gpus, pairs_per_set=4096, steps=300, batch=1024, lr=1e-3, seed=5)
+    assert np.all(np.isfinite(curve))
+    assert curve[-30:].mean() < 0.5 * curve[:10].mean()
+
+
+def test_propose_and_random_search_are_exact(ko):
+    s = synth.gen_set("large", 3)
+    m = ko.Model(seed=1)
+    with ko.Gpu.from_set(s) as g:
+        order, ms, t_ms = m.propose(g, n_cand=70000, top_k=256, seed=9)
+        assert sorted(order.tolist()) == list(range(s.n)) and t_ms > 0
+        assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
+        ro, rms, _ = ko.ko_random_search(g, 5000, seed=4)
+        assert sorted(ro.tolist()) == list(range(s.n))
+        assert rms == oracle.makespan(s.gpu, s.kernels, ro.tolist())
