@@ -293,6 +293,33 @@ ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *
 
 void ko_model_destroy(ko_model *m);
 
+/* ------------------------------------------------ allocation-free evaluation
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code running under a
+ * memory manager that owns the whole device heap (a framework's caching
+ * allocator that has reserved the GPU), or latency-critical code that must
+ * not call cudaMalloc / cudaFree because those calls can synchronise the
+ * device.  ko_eval_orders_noalloc computes what ko_eval_orders computes for
+ * explicit rows (same makespans, -1 for a row that is not a permutation),
+ * using the simple one-thread-per-order simulator, and allocates nothing: its
+ * per-thread simulator state lives in a file-scope device array of 32 MiB
+ * that every GPU which loads the library holds until the process exits.
+ *   orders        n x N kernel ids (int8, row-major), device memory
+ *   makespan_out  n int64, device memory
+ * Host pointers are rejected (KO_ERR_ARG): staging them would need device
+ * memory.  The array holds at least 128 threads' state, so a set whose
+ * per-thread state, N_SM x (36 + 12 N_blk_SM) bytes rounded up to 256, exceeds
+ * 262,144 bytes (for example N_SM > 624 at 32 blocks per SM) is rejected with
+ * KO_ERR_TOO_LARGE.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and uses it as
+ * scratch only (nothing carries over between calls), so calls that overlap
+ * on the GPU -- concurrent streams, or other host threads -- race on it:
+ * serialise them.  Asynchronous on `stream`. */
+ko_status ko_eval_orders_noalloc(const ko_gpu *g, const int8_t *orders, int64_t n,
+                                 int64_t *makespan_out, void *stream);
+
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);
 

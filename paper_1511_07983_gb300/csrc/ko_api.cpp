@@ -736,6 +736,16 @@ ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *
 
 void ko_model_destroy(ko_model *m) { ko_model_free(m); }
 
+ko_status ko_eval_orders_noalloc(const ko_gpu *g, const int8_t *orders, int64_t n, int64_t *makespan_out,
+                                 void *stream)
+{
+    if (!g || n < 0 || g->h.n < 1 || (n > 0 && (!orders || !makespan_out))) return fail(KO_ERR_ARG);
+    if (n == 0) return ok();
+    if (!is_device_ptr(orders) || !is_device_ptr(makespan_out)) return fail(KO_ERR_ARG);
+    ko_status s = ko_noalloc_eval(g->h, orders, n, makespan_out, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
 void ko_destroy_gpu(ko_gpu *g) { delete g; }
 
 const char *ko_status_str(ko_status s)

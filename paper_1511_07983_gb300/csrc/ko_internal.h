@@ -88,6 +88,13 @@ ko_status ko_random_search_set(KoFastState *fs, const KoSet &h, long long n_orde
                                int32_t *best_order, int64_t *best_makespan, double *gpu_ms, cudaStream_t st);
 ko_status ko_model_features(const KoSet &h, const int8_t *orders, long long n, float *x_out, cudaStream_t st);
 
+// Allocation-free evaluation (ko_sim_simple.cu): explicit device rows, scratch
+// in a file-scope device array.
+constexpr int KO_MAX_DEVICES = 64;
+ko_status ko_noalloc_eval(const KoSet &h, const int8_t *d_orders, long long count, int64_t *d_out,
+                          cudaStream_t st);
+size_t ko_noalloc_scratch_bytes();
+
 // Host-side Algorithm 1; returns the number of execution rounds.
 int ko_heuristic_host(const KoSet &h, int32_t *order_out);
 

@@ -17,6 +17,8 @@
 //           before the next burst; the makespan is the last end.
 // Blocks of one kernel that start together on one SM share their end time and
 // are kept as one group (kernel, count, end).
+#include <mutex>
+
 #include "ko_internal.h"
 #include "ko_fast.h"
 
@@ -354,6 +356,33 @@ fallback_kernel(KoWork w, void *scratch, size_t per_thread)
     }
 }
 
+// Variant of simple_kernel for the allocation-free entry point: the set comes
+// by value as a kernel parameter and the per-thread slabs live in the
+// file-scope array below (its device address is passed in).
+__global__ void __launch_bounds__(kThreads)
+simple_static_kernel(const KoSet set, const int8_t *__restrict__ perms, long long count,
+                     int64_t *__restrict__ out, void *scratch, size_t per_thread)
+{
+    __shared__ KoSet sd;
+    if (threadIdx.x == 0) sd = set;
+    __syncthreads();
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const Slab st = slab_at(scratch, per_thread, sd.S, sd.Bk, slot);
+    const int n = sd.n;
+    for (long long j = slot; j < count; j += (long long)gridDim.x * blockDim.x) {
+        int8_t perm[KO_MAX_KERNELS];
+        bool ok = true;
+        uint32_t seen = 0;
+        for (int q = 0; q < n; q++) {
+            const int v = perms[j * n + q];
+            if (v < 0 || v >= n || ((seen >> v) & 1u)) ok = false;
+            else seen |= 1u << v;
+            perm[q] = (int8_t)(v < 0 || v >= n ? 0 : v);
+        }
+        out[j] = ok ? simulate(sd, perm, st) : -1;
+    }
+}
+
 constexpr int kHistThreads = 256;
 
 __global__ void __launch_bounds__(kHistThreads)
@@ -391,6 +420,62 @@ __global__ void accum_reset_kernel(KoAccum *acc, int count)
 }
 
 }  // namespace
+
+// ------------------------------------------------- allocation-free evaluation
+// Scratch of ko_eval_orders_noalloc: per-thread simulator slabs, shared by
+// every call in the process and held on every device that loads the library.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[KO_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the name is only a host-side stand-in for the device symbol).
+ko_status noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= KO_MAX_DEVICES) {
+        cudaGetLastError();
+        return KO_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return KO_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return KO_OK;
+}
+
+}  // namespace
+
+ko_status ko_noalloc_eval(const KoSet &h, const int8_t *d_orders, long long count, int64_t *d_out,
+                          cudaStream_t st)
+{
+    const size_t per = slab_bytes(h.S, h.Bk);
+    const long long slots = (long long)(kNoAllocScratchBytes / per);
+    if (slots < kThreads) return KO_ERR_TOO_LARGE;  // the set's simulator state exceeds the array
+    if (count <= 0) return KO_OK;
+    void *scratch = nullptr;
+    ko_status s = noalloc_scratch(&scratch);
+    if (s) return s;
+    long long blocks = slots / kThreads;
+    const long long need = (count + kThreads - 1) / kThreads;
+    if (blocks > need) blocks = need;
+    simple_static_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(h, d_orders, count, d_out, scratch, per);
+    ko_count_launch();
+    if (cudaGetLastError() != cudaSuccess) return KO_ERR_CUDA;
+    return KO_OK;
+}
+
+size_t ko_noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
 
 size_t ko_simple_scratch_per_thread(const KoSet &h) { return slab_bytes(h.S, h.Bk); }
 

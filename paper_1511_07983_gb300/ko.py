@@ -90,6 +90,8 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
+    "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "ko_destroy_gpu": (None, [ctypes.c_void_p]),
     "ko_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "ko_last_error": (ctypes.c_int32, []),
