@@ -52,6 +52,10 @@ def args_parse():
                     help="use only the first n kernels of the set (small profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=300000,
                     help="orders in the oracle's bounded CPU sample")
+    ap.add_argument("--surrogate", type=int, default=1,
+                    help="1: also run the surrogate-vs-plain comparison (outside the timed region)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick lanes / DFS depth with ko_autotune before warm-up")
     return ap.parse_args()
 
 
@@ -111,6 +115,21 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(seconds: float, dist) -> float:
+    """Slowest rank's time (a gloo all-reduce of one float; no data path)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(orders_per_replica: int, steps: int, world: int, seconds: float) -> float:
+    """Orders all ranks scored divided by the slowest rank's time (replicas)."""
+    return orders_per_replica * steps * world / seconds
 
 
 def placements_per_exhaustive(kernels) -> int:
@@ -202,8 +221,14 @@ def run_ours(a):
     kset = load_set(a)
     n_orders = math.factorial(kset.n)
     g = ko.Gpu.from_set(kset)
+    tune = None
     if a.lanes or a.levels is not None:
         g.configure(lanes=a.lanes, levels=a.levels)
+    elif a.autotune:
+        t0 = time.perf_counter()
+        choice = g.autotune(os.path.join(tempfile.gettempdir(), "ko_autotune.json"))
+        tune = {"lanes": choice["lanes"], "levels": choice["levels"],
+                "seconds": round(time.perf_counter() - t0, 2)}
     stream = torch.cuda.current_stream()
     d_hist = torch.zeros(NBINS, dtype=torch.int64, device="cuda")   # uint64 bits
     h_hist = np.zeros(NBINS, dtype=np.uint64)
@@ -236,11 +261,7 @@ def run_ours(a):
     clk = clocks.stop()
     launches = ko.ko_kernel_launches() - launches0
     barrier()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
     # end-to-end through the same call with host buffers
     h2d0, d2h0 = g.transfer_bytes()
@@ -250,12 +271,8 @@ def run_ours(a):
     for _ in range(a.steps):
         step(True)
     torch.cuda.synchronize()
-    e2e_elapsed = time.perf_counter() - t0
+    e2e_elapsed = max_over_ranks(time.perf_counter() - t0, dist)
     h2d1, d2h1 = g.transfer_bytes()
-    if dist:
-        t = torch.tensor([e2e_elapsed], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_elapsed = float(t.item())
 
     if rank != 0:
         g.close()
@@ -263,7 +280,7 @@ def run_ours(a):
             dist.destroy_process_group()
         return 0
 
-    value = n_orders * a.steps * world / elapsed
+    value = whole_job_rate(n_orders, a.steps, world, elapsed)
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -279,6 +296,7 @@ def run_ours(a):
         except ValueError:
             traffic = None
     cb = cpu_baseline(kset, a.cpu_sample) if world == 1 else None
+    sur = surrogate_experiment() if (a.surrogate and world == 1) else None
     line = {
         "metric": METRIC, "value": value, "unit": "orders/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps,
@@ -290,19 +308,21 @@ def run_ours(a):
                                f"histogram + heuristic rank",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB flush before every step; the 3.8 GB makespan buffer exceeds L2",
-                   "lanes": g_opt(g, "lanes", a.lanes), "levels": g_opt(g, "levels", a.levels)},
+                   "lanes": ko.ko_get_option(g.h, ko.KO_OPT_LANES),
+                   "levels": ko.ko_get_option(g.h, ko.KO_OPT_LEVELS), "autotune": tune},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "fast_kernel", "kernel_ms": kernel_s * 1e3,
                      "placements_per_launch": placements, "ops_per_placement": OPS_PER_PLACEMENT,
                      "peak_from": f"{sm_count} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz"},
         "cpu_baseline": cb,
-        "e2e": {"value": n_orders * a.steps * world / e2e_elapsed, "unit": "orders/s",
+        "e2e": {"value": whole_job_rate(n_orders, a.steps, world, e2e_elapsed), "unit": "orders/s",
                 "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,
                 "d2h_bytes_per_step": (d2h1 - d2h0) // a.steps},
         "gpu_launches": launches,
         "clocks": clk,
         "fallback_items_per_step": max(fallback) if fallback else 0,
+        "surrogate": sur,
         "heuristic": {"makespan": r["makespan"], "percentile": r["percentile"],
                       "min": r["min"], "max": r["max"]},
     }
@@ -313,10 +333,61 @@ def run_ours(a):
     return 0
 
 
-def g_opt(g, name, given):
-    if given is not None:
-        return given
-    return {"lanes": 32, "levels": 4}[name]
+def percentile_of(best, ref):
+    """Share (%) of the reference orders at least as slow as `best`."""
+    import numpy as np
+    return 100.0 * float(np.count_nonzero(ref >= best)) / ref.size
+
+
+def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4096,
+                         test_sets=8, n_cand=1 << 22, top_k=1024, ref_orders=1 << 20):
+    """Surrogate-guided search vs plain random-order search at equal GPU time.
+
+    The model is trained on simulator-labelled uniform orders of seeded sets
+    (N 6..12 and N 16..24, different seeds from the test sets); on each held-out
+    set with N in 16..24 the surrogate screens n_cand random candidates and
+    rescores its top_k exactly; plain search then simulates as many uniform
+    orders as fit in the surrogate's measured GPU time.  Both best makespans are
+    ranked against the exact makespans of ref_orders seeded uniform orders."""
+    import numpy as np
+    from paper_1511_07983_gb300 import ko, synth
+    t0 = time.perf_counter()
+    train = [synth.gen_set("train", 1000 + i) for i in range(train_sets // 2)]
+    train += [synth.gen_set("large", 1000 + i) for i in range(train_sets - train_sets // 2)]
+    gpus = [ko.Gpu.from_set(k) for k in train]
+    model = ko.Model(seed=seed)
+    curve = model.train(gpus, pairs_per_set=pairs, steps=steps, batch=batch, lr=1e-3, seed=seed)
+    for g in gpus:
+        g.close()
+    train_s = time.perf_counter() - t0
+    rows = []
+    rng = np.random.default_rng(seed)
+    for j in range(test_sets):
+        ks = synth.gen_set("large", j)
+        with ko.Gpu.from_set(ks) as g:
+            ref_rows = np.argsort(rng.random((ref_orders, ks.n)), axis=1).astype(np.int8)
+            ref = g.eval_orders(orders=ref_rows)
+            _, s_best, s_ms = model.propose(g, n_cand=n_cand, top_k=top_k, seed=seed + j)
+            _, _, cal_ms = ko.ko_random_search(g, 1 << 16, seed=99 + j)
+            n_plain = max(1, int((1 << 16) * s_ms / max(cal_ms, 1e-3)))
+            _, p_best, p_ms = ko.ko_random_search(g, n_plain, seed=seed + 100 + j)
+            h_ms = int(g.eval_orders(orders=np.array([g.heuristic_order()], dtype=np.int8))[0])
+            rows.append({"n": ks.n, "n_sm": ks.gpu[0], "surrogate_ms": s_ms, "plain_ms": p_ms,
+                         "plain_orders": n_plain,
+                         "surrogate_pct": percentile_of(s_best, ref),
+                         "plain_pct": percentile_of(p_best, ref),
+                         "heuristic_pct": percentile_of(h_ms, ref)})
+    model.close()
+    mean = lambda k: sum(r[k] for r in rows) / len(rows)
+    return {"test_sets": len(rows), "train_pairs": train_sets * pairs, "train_steps": steps,
+            "train_s": round(train_s, 2), "final_loss": float(curve[-50:].mean()),
+            "candidates": n_cand, "top_k": top_k, "reference_orders": ref_orders,
+            "surrogate_percentile_mean": mean("surrogate_pct"),
+            "plain_percentile_mean": mean("plain_pct"),
+            "heuristic_percentile_mean": mean("heuristic_pct"),
+            "surrogate_wins": sum(r["surrogate_pct"] > r["plain_pct"] for r in rows),
+            "ties": sum(r["surrogate_pct"] == r["plain_pct"] for r in rows),
+            "per_set": rows}
 
 
 def main():

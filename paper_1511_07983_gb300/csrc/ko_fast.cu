@@ -336,36 +336,49 @@ struct Sim {
         return t + (long long)dmax;
     }
 
-    __device__ void save(int *slot) const
+    // Save / restore the node state; only the first SAVE lanes are stored, so
+    // a node with more runs than that abandons the work item.
+    template <int SAVE>
+    __device__ void save(int *slot)
     {
-        int *q = slot + sg.lane;
-        q[0 * LANES] = run.beg; q[1 * LANES] = run.cnt; q[2 * LANES] = run.ur;
-        q[3 * LANES] = run.us; q[4 * LANES] = run.uw; q[5 * LANES] = run.ub;
-        q[6 * LANES] = run.sc; q[7 * LANES] = run.sm;
+        if (nruns > SAVE) { fail = 1; return; }
+        if (sg.lane < SAVE) {
+            int *q = slot + sg.lane;
+            q[0 * SAVE] = run.beg; q[1 * SAVE] = run.cnt; q[2 * SAVE] = run.ur;
+            q[3 * SAVE] = run.us; q[4 * SAVE] = run.uw; q[5 * SAVE] = run.ub;
+            q[6 * SAVE] = run.sc; q[7 * SAVE] = run.sm;
 #pragma unroll
-        for (int g = 0; g < kG; g++) {
-            q[(8 + g) * LANES] = (int)run.gk[g];
-            q[(8 + kG + g) * LANES] = (int)run.ge[g];
+            for (int g = 0; g < kG; g++) {
+                q[(8 + g) * SAVE] = (int)run.gk[g];
+                q[(8 + kG + g) * SAVE] = (int)run.ge[g];
+            }
         }
         if (sg.lane == 0) {
-            int *u = slot + kStateWords * LANES;
+            int *u = slot + kStateWords * SAVE;
             u[0] = (int)(t & 0xffffffffll); u[1] = (int)(t >> 32); u[2] = p; u[3] = nruns;
         }
         __syncwarp(sg.mask);
     }
 
+    template <int SAVE>
     __device__ void restore(const int *slot)
     {
-        const int *q = slot + sg.lane;
-        run.beg = q[0 * LANES]; run.cnt = q[1 * LANES]; run.ur = q[2 * LANES];
-        run.us = q[3 * LANES]; run.uw = q[4 * LANES]; run.ub = q[5 * LANES];
-        run.sc = q[6 * LANES]; run.sm = q[7 * LANES];
+        if (sg.lane < SAVE) {
+            const int *q = slot + sg.lane;
+            run.beg = q[0 * SAVE]; run.cnt = q[1 * SAVE]; run.ur = q[2 * SAVE];
+            run.us = q[3 * SAVE]; run.uw = q[4 * SAVE]; run.ub = q[5 * SAVE];
+            run.sc = q[6 * SAVE]; run.sm = q[7 * SAVE];
 #pragma unroll
-        for (int g = 0; g < kG; g++) {
-            run.gk[g] = (uint32_t)q[(8 + g) * LANES];
-            run.ge[g] = (uint32_t)q[(8 + kG + g) * LANES];
+            for (int g = 0; g < kG; g++) {
+                run.gk[g] = (uint32_t)q[(8 + g) * SAVE];
+                run.ge[g] = (uint32_t)q[(8 + kG + g) * SAVE];
+            }
+        } else {
+            run.beg = 0; run.cnt = 0; run.ur = run.us = run.uw = run.ub = run.sc = run.sm = 0;
+#pragma unroll
+            for (int g = 0; g < kG; g++) { run.gk[g] = 0; run.ge[g] = 0; }
         }
-        const int *u = slot + kStateWords * LANES;
+        const int *u = slot + kStateWords * SAVE;
         t = (long long)(uint32_t)u[0] | ((long long)u[1] << 32);
         p = u[2];
         nruns = u[3];
@@ -439,8 +452,12 @@ struct SegStats {
     }
 };
 
-template <int LANES, int G>
-__global__ void __launch_bounds__(kThreads)
+#ifndef KO_FAST_MIN_BLOCKS
+#define KO_FAST_MIN_BLOCKS 1   // resident blocks per SM the register budget must allow
+#endif
+
+template <int LANES, int G, int SAVE>
+__global__ void __launch_bounds__(kThreads, KO_FAST_MIN_BLOCKS)
 fast_kernel(KoWork a)
 {
     constexpr int kStateWords = state_words(G);
@@ -453,7 +470,7 @@ fast_kernel(KoWork a)
     sim.sg.lane = threadIdx.x % LANES;
     sim.run_limit = a.run_limit < LANES ? a.run_limit : LANES;
     sim.sg.mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
-    const int level_words = kStateWords * LANES + 4;
+    const int level_words = kStateWords * SAVE + 4;
     int *stack = stack_mem + seg * a.levels * level_words;
     SetConst &K = Ks[seg];
     int loaded = -1;
@@ -480,14 +497,16 @@ fast_kernel(KoWork a)
             st.set = ch.set;
         }
         const int n = K.n;
+        const uint32_t all = (1u << n) - 1u;
         const long long ref = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
         const long long local = (long long)item - ch.first;
 
+        // perm[0 .. d0) is the item's fixed prefix (the whole order in list modes)
         int8_t perm[KO_MAX_KERNELS];
-        uint32_t used = 0;
         int d0;
         long long outpos;
         bool valid = true;
+        uint32_t used = 0;
         if (ch.mode == 1) {
             d0 = n;
             outpos = ch.out_off + local;
@@ -514,63 +533,63 @@ fast_kernel(KoWork a)
             if (sim.sg.lane == 0 && a.out) a.out[outpos] = -1;
             continue;
         }
-        sim.init(K);
-        for (int j = 0; j < d0 && !sim.fail; j++) sim.place_kernel(K, perm[j]);
 
+        // One walk per item: depths below d0 take the prefix kernel, depths from
+        // d0 on enumerate the unused kernels in increasing id (lexicographic DFS),
+        // restoring the saved node state for every child after the first.
         unsigned long long imin = ~0ull, imax = 0, ib = 0, ie = 0, iw = 0;
         long long leaf = 0;
-        if (d0 == n) {
-            if (!sim.fail) {
-                const long long ms = sim.finish(K);
-                if (sim.sg.lane == 0) {
-                    if (a.out) a.out[outpos] = ms;
-                    imin = imax = (unsigned long long)ms;
-                    ib = ms < ref; ie = ms == ref; iw = ms > ref;
-                }
-            }
-        } else {
-            // lexicographic DFS below the prefix; node states saved per depth
-            int depth = d0;
-            int next[KO_MAX_KERNELS + 1];
-            next[depth] = 0;
-            bool first_child = true;
-            if (!sim.fail && n - depth >= 2) sim.save(stack + (depth - d0) * level_words);
-            while (!sim.fail) {
-                const uint32_t avail = ~used & ((1u << n) - 1u) & ~((1u << next[depth]) - 1u);
+        int next[KO_MAX_KERNELS + 1];
+        int depth = 0;
+        bool first_child = true;
+        used = 0;
+        sim.init(K);
+        if (d0 == 0) {
+            next[0] = 0;
+            if (n >= 2) sim.template save<SAVE>(stack);
+        }
+        while (!sim.fail) {
+            int cand;
+            if (depth < d0) {
+                cand = perm[depth];
+            } else {
+                const uint32_t avail = ~used & all & ~((1u << next[depth]) - 1u);
                 if (avail == 0) {
                     if (depth == d0) break;
                     depth--;
-                    const int prev = perm[depth];
-                    used &= ~(1u << prev);
-                    next[depth] = prev + 1;
+                    used &= ~(1u << perm[depth]);
+                    next[depth] = perm[depth] + 1;
                     first_child = false;
                     continue;
                 }
-                const int cand = __ffs(avail) - 1;
-                if (!first_child) sim.restore(stack + (depth - d0) * level_words);
-                perm[depth] = (int8_t)cand;
-                used |= 1u << cand;
-                sim.place_kernel(K, cand);
-                if (sim.fail) break;
-                if (depth + 1 == n) {
-                    const long long ms = sim.finish(K);
-                    if (sim.sg.lane == 0) {
-                        if (a.out) a.out[outpos + leaf] = ms;
-                        const unsigned long long u = (unsigned long long)ms;
-                        imin = u < imin ? u : imin;
-                        imax = u > imax ? u : imax;
-                        ib += ms < ref; ie += ms == ref; iw += ms > ref;
-                    }
-                    leaf++;
-                    used &= ~(1u << cand);
-                    next[depth] = cand + 1;
-                    first_child = false;
-                    continue;
+                cand = __ffs(avail) - 1;
+                if (!first_child) sim.template restore<SAVE>(stack + (depth - d0) * level_words);
+            }
+            perm[depth] = (int8_t)cand;
+            used |= 1u << cand;
+            sim.place_kernel(K, cand);
+            if (sim.fail) break;
+            if (depth + 1 == n) {
+                const long long ms = sim.finish(K);
+                if (sim.sg.lane == 0) {
+                    if (a.out) a.out[outpos + leaf] = ms;
+                    const unsigned long long u = (unsigned long long)ms;
+                    imin = u < imin ? u : imin;
+                    imax = u > imax ? u : imax;
+                    ib += ms < ref; ie += ms == ref; iw += ms > ref;
                 }
-                depth++;
+                leaf++;
+                if (d0 == n) break;
+                used &= ~(1u << cand);
+                next[depth] = cand + 1;
+                first_child = false;
+                continue;
+            }
+            depth++;
+            if (depth >= d0) {
                 next[depth] = 0;
                 first_child = true;
-                if (n - depth >= 2) sim.save(stack + (depth - d0) * level_words);
+                if (n - depth >= 2) sim.template save<SAVE>(stack + (depth - d0) * level_words);
             }
         }
         if (sim.fail) {
@@ -597,25 +616,25 @@ constexpr unsigned long long kOvCap = 1 << 20;
 constexpr size_t kFallbackScratch = size_t(256) << 20;
 
 
-template <int LANES, int G>
+template <int LANES, int G, int SAVE>
 cudaError_t launch(const KoWork &a, cudaStream_t st)
 {
-    const int level_words = state_words(G) * LANES + 4;
+    const int level_words = state_words(G) * SAVE + 4;
     const size_t smem = sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
-    cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES, G, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES, G>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES, G, SAVE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
     const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
     const long long blocks_needed = (work + kThreads / LANES - 1) / (kThreads / LANES);
     if (blocks > blocks_needed) blocks = blocks_needed;
     if (blocks < 1) blocks = 1;
-    fast_kernel<LANES, G><<<(unsigned)blocks, kThreads, smem, st>>>(a);
+    fast_kernel<LANES, G, SAVE><<<(unsigned)blocks, kThreads, smem, st>>>(a);
     ko_count_launch();
     return cudaGetLastError();
 }
@@ -677,7 +696,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w.ov_list = fb->ov_list;
     w.item_list = nullptr;
     w.item_count = nullptr;
-    cudaError_t e = fs->lanes == 16 ? launch<16, kG>(w, st) : launch<32, kG>(w, st);
+    cudaError_t e = fs->lanes == 16 ? launch<16, kG, 16>(w, st) : launch<32, kG, 16>(w, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_CUDA;
@@ -690,7 +709,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w2.ov_count = &fb->ov_count[1];
     w2.ov_list = fb->ov_list + kOvCap;
     w2.run_limit = fs->run_limit;
-    e = launch<32, kGWide>(w2, st);
+    e = launch<32, kGWide, 32>(w2, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_CUDA;

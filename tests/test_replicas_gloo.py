@@ -1,0 +1,53 @@
+"""Multi-rank host logic of bench.py on CPU: world_size 2 over gloo (no GPU).
+bench.py runs one independent replica per rank; only the barrier and the max
+of the per-rank times cross ranks."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.barrier()
+    slowest = bench.max_over_ranks(1.5 + rank, dist)     # rank 1 is the slow one
+    q.put((rank, slowest, bench.whole_job_rate(1000, 2, world, slowest), bench.dist_env()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_max_time_and_sum_work():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, slowest, rate, env in out:
+        assert slowest == 2.5
+        assert rate == pytest.approx(1000 * 2 * 2 / 2.5)
+        assert env == (rank, 2, rank)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert bench.main() == 0
+    assert capsys.readouterr().out == ""
