@@ -296,7 +296,12 @@ def run_ours(a):
         except ValueError:
             traffic = None
     cb = cpu_baseline(kset, a.cpu_sample) if world == 1 else None
-    sur = surrogate_experiment() if (a.surrogate and world == 1) else None
+    sur = None
+    if a.surrogate and world == 1:
+        try:
+            sur = surrogate_experiment()
+        except Exception as exc:  # reported, never fatal to the bench line
+            sur = {"error": f"{type(exc).__name__}: {exc}"}
     line = {
         "metric": METRIC, "value": value, "unit": "orders/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps,
