@@ -452,8 +452,11 @@ struct SegStats {
     }
 };
 
+// Resident blocks per SM the register budget must allow.  8 blocks (64
+// registers, a few spills to L1) measured fastest on the N=12 / 148-SM set:
+// the kernel is latency-bound and extra warps hide more than the spills cost.
 #ifndef KO_FAST_MIN_BLOCKS
-#define KO_FAST_MIN_BLOCKS 1   // resident blocks per SM the register budget must allow
+#define KO_FAST_MIN_BLOCKS 8
 #endif
 
 template <int LANES, int G, int SAVE>

@@ -77,3 +77,40 @@ def test_batch_rejects_large_sets(ko):
     with pytest.raises(ko.KoError) as e:
         ko.Batch([ko.Gpu.from_set(s)])
     assert e.value.code == -3
+
+
+def _check_full_batch(ko, sets, res, hist, nbins, cross):
+    for i, (s, r) in enumerate(zip(sets, res)):
+        total = math.factorial(s.n)
+        assert r["n_total"] == total
+        assert r["n_better"] + r["n_equal"] + r["n_worse"] == total and r["n_equal"] >= 1
+        h = oracle.heuristic(s.gpu, s.kernels)
+        assert r["makespan"] == oracle.makespan(s.gpu, s.kernels, h), i
+        lb, ub = oracle.bounds(s.gpu, s.kernels)
+        assert lb <= r["min"] <= r["makespan"] <= r["max"] <= ub
+        if hist is not None:
+            assert int(hist[i].sum()) == total and hist[i][0] >= 1
+    for i in cross:   # single-set path on the same set (oracle-checked elsewhere)
+        with ko.Gpu.from_set(sets[i]) as g:
+            one, h1 = g.rank_order(None, nbins=nbins or 1)
+        for k in ("min", "max", "makespan", "n_better", "n_equal", "n_worse"):
+            assert res[i][k] == one[k], (i, k)
+        if hist is not None:
+            assert np.array_equal(hist[i], h1)
+
+
+def test_sixty_four_n10_sets_with_histograms(ko):
+    """All 64 N=10 sets (15-SM GPU), 232,243,200 orders, one captured graph."""
+    sets = [synth.gen_set("sets10", i) for i in range(64)]
+    b = ko.Batch([ko.Gpu.from_set(s) for s in sets], nbins=4096)
+    res, hist = b.run()
+    assert b.orders() == 64 * math.factorial(10)
+    _check_full_batch(ko, sets, res, hist, 4096, cross=(0, 17, 63))
+
+
+def test_mixed_batch_first_512_sets(ko):
+    """First 512 of the 4096 mixed sets (N 5..10, 13/15/148 SMs)."""
+    sets = [synth.gen_set("batched", i) for i in range(512)]
+    b = ko.Batch([ko.Gpu.from_set(s) for s in sets], nbins=0)
+    res, _ = b.run()
+    _check_full_batch(ko, sets, res, None, 0, cross=(1, 200, 511))
