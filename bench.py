@@ -226,7 +226,7 @@ def run_ours(a):
         g.configure(lanes=a.lanes, levels=a.levels)
     elif a.autotune:
         t0 = time.perf_counter()
-        choice = g.autotune(os.path.join(tempfile.gettempdir(), "ko_autotune.json"))
+        choice = g.autotune(os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"))
         tune = {"lanes": choice["lanes"], "levels": choice["levels"],
                 "seconds": round(time.perf_counter() - t0, 2)}
     stream = torch.cuda.current_stream()
@@ -345,14 +345,17 @@ def percentile_of(best, ref):
 
 
 def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4096,
-                         test_sets=8, n_cand=1 << 22, top_k=1024, ref_orders=1 << 20):
+                         test_sets=8, n_cand=1 << 20, top_k=1024, rounds=12, beam=8,
+                         ref_orders=1 << 20):
     """Surrogate-guided search vs plain random-order search at equal GPU time.
 
     The model is trained on simulator-labelled uniform orders of seeded sets
     (N 6..12 and N 16..24, different seeds from the test sets); on each held-out
-    set with N in 16..24 the surrogate screens n_cand random candidates and
-    rescores its top_k exactly; plain search then simulates as many uniform
-    orders as fit in the surrogate's measured GPU time.  Both best makespans are
+    set with N in 16..24 the surrogate screens n_cand random candidates,
+    rescores its top_k exactly and then runs `rounds` of network-ranked local
+    search around a beam of the best exact orders (ko_surrogate_search); plain
+    search simulates as many uniform orders as fit in the surrogate's measured
+    GPU time.  Both best makespans are
     ranked against the exact makespans of ref_orders seeded uniform orders."""
     import numpy as np
     from paper_1511_07983_gb300 import ko, synth
@@ -372,7 +375,8 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
         with ko.Gpu.from_set(ks) as g:
             ref_rows = np.argsort(rng.random((ref_orders, ks.n)), axis=1).astype(np.int8)
             ref = g.eval_orders(orders=ref_rows)
-            _, s_best, s_ms = model.propose(g, n_cand=n_cand, top_k=top_k, seed=seed + j)
+            _, s_best, s_ms = model.search(g, n_cand=n_cand, top_k=top_k, rounds=rounds, beam=beam,
+                                           seed=seed + j)
             _, _, cal_ms = ko.ko_random_search(g, 1 << 16, seed=99 + j)
             n_plain = max(1, int((1 << 16) * s_ms / max(cal_ms, 1e-3)))
             _, p_best, p_ms = ko.ko_random_search(g, n_plain, seed=seed + 100 + j)
@@ -386,7 +390,8 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
     mean = lambda k: sum(r[k] for r in rows) / len(rows)
     return {"test_sets": len(rows), "train_pairs": train_sets * pairs, "train_steps": steps,
             "train_s": round(train_s, 2), "final_loss": float(curve[-50:].mean()),
-            "candidates": n_cand, "top_k": top_k, "reference_orders": ref_orders,
+            "candidates": n_cand, "top_k": top_k, "rounds": rounds, "beam": beam,
+            "reference_orders": ref_orders,
             "surrogate_percentile_mean": mean("surrogate_pct"),
             "plain_percentile_mean": mean("plain_pct"),
             "heuristic_percentile_mean": mean("heuristic_pct"),

@@ -171,9 +171,10 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 int64_t ko_get_option(const ko_gpu *g, int32_t key);
 
 /* Autotuner: times the run-length simulator on a calibration slice of this
- * set's exhaustive space for every candidate (16 or 32 lanes per simulation;
- * 1..min(N-1, 6) saved DFS levels, skipping depths that leave too few work
- * items), keeps the fastest and sets KO_OPT_LANES / KO_OPT_LEVELS on the
+ * set's exhaustive space (about 4M orders, at least 20k work items) for every
+ * candidate (16 or 32 lanes per simulation; 1..min(N-1, 5) saved DFS levels,
+ * skipping depths whose slice would exceed 40M orders), keeps the fastest
+ * and sets KO_OPT_LANES / KO_OPT_LEVELS on the
  * handle.  With cache_path (nullable) the choice is looked up first and
  * stored after, keyed by (N_SM class, N), in a small JSON file.  Synchronises
  * `stream`; results never depend on the choice.  N <= 12. */
@@ -286,10 +287,31 @@ ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t t
                                int32_t *best_order, int64_t *best_makespan, double *gpu_ms,
                                void *stream);
 
+/* Surrogate-guided local search for a set with 2 <= N <= 24.  Screening as
+ * in ko_surrogate_propose (n_cand candidates, top_k rescored exactly) seeds a
+ * beam of the `beam` (1..64) best exact orders; each of `rounds` (0..1024)
+ * rounds scores every swap of two positions and every move of one kernel to
+ * another position of each beam order with the network, rescores the 256
+ * best exactly and keeps the `beam` best distinct orders.  Returns the best
+ * exact order found (host, N ids); gpu_ms = device-timeline duration of the
+ * whole search including the host's per-round bookkeeping. */
+ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, int32_t rounds,
+                              int32_t beam, uint64_t seed, int32_t *best_order, int64_t *best_makespan,
+                              double *gpu_ms, void *stream);
+
 /* Plain random search, the baseline of the surrogate: n_orders uniform random
  * orders simulated exactly; the best one is returned. */
 ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
                            int64_t *best_makespan, double *gpu_ms, void *stream);
+
+/* Model options.  KO_MODEL_OPT_TC: tensor-core path of the inference
+ * forward (ko_model_predict, ko_surrogate_propose) -- 0 = warp-level
+ * mma.sync BF16 GEMMs (default), 1 = tcgen05 MMAs with TMEM accumulators
+ * (batches padded to multiples of 128).  A tcgen05 completion wait that
+ * gives up makes the next call return KO_ERR_TIMEOUT.  Training always uses
+ * mma.sync.  KO_ERR_ARG for an unknown key or value. */
+#define KO_MODEL_OPT_TC 1
+ko_status ko_model_set_option(ko_model *m, int32_t key, int64_t value);
 
 void ko_model_destroy(ko_model *m);
 

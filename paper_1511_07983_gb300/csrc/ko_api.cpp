@@ -724,6 +724,17 @@ ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t t
     return s ? fail(s) : ok();
 }
 
+ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, int32_t rounds,
+                              int32_t beam, uint64_t seed, int32_t *best_order, int64_t *best_makespan,
+                              double *gpu_ms, void *stream)
+{
+    if (!m || !g || !best_order || !best_makespan || g->h.n < 2) return fail(KO_ERR_ARG);
+    g->frozen = true;
+    ko_status s = ko_model_search_set(m, g->h, n_cand, top_k, rounds, beam, seed, best_order, best_makespan,
+                                      gpu_ms, (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
 ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
                            int64_t *best_makespan, double *gpu_ms, void *stream)
 {
@@ -731,6 +742,13 @@ ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *
     g->frozen = true;
     ko_status s = ko_random_search_set(&g->fast, g->h, n_orders, seed, best_order, best_makespan, gpu_ms,
                                        (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_model_set_option(ko_model *m, int32_t key, int64_t value)
+{
+    if (!m) return fail(KO_ERR_ARG);
+    ko_status s = ko_model_option(m, key, value);
     return s ? fail(s) : ok();
 }
 

@@ -78,12 +78,16 @@ ko_model *ko_model_new(uint64_t seed, ko_status *err);
 ko_status ko_model_load(ko_model *md, const float *params);
 ko_status ko_model_store(const ko_model *md, float *params);
 void ko_model_free(ko_model *md);
+ko_status ko_model_option(ko_model *md, int key, long long value);
 ko_status ko_model_raw(ko_model *md, const float *x, const float *t, int B, float *y_out, float *grad_out,
                        float *loss_out, float lr, cudaStream_t st);
 ko_status ko_model_train_sets(ko_model *md, const KoSet *const *hs, int nsets, long long pairs_per_set,
                               int steps, int batch, float lr, uint64_t seed, float *loss_curve, cudaStream_t st);
 ko_status ko_model_propose_set(ko_model *md, const KoSet &h, long long n_cand, int top_k, uint64_t seed,
                                int32_t *best_order, int64_t *best_makespan, double *gpu_ms, cudaStream_t st);
+ko_status ko_model_search_set(ko_model *md, const KoSet &h, long long n_cand, int top_k, int rounds, int beam,
+                              uint64_t seed, int32_t *best_order, int64_t *best_makespan, double *gpu_ms,
+                              cudaStream_t st);
 ko_status ko_random_search_set(KoFastState *fs, const KoSet &h, long long n_orders, uint64_t seed,
                                int32_t *best_order, int64_t *best_makespan, double *gpu_ms, cudaStream_t st);
 ko_status ko_model_features(const KoSet &h, const int8_t *orders, long long n, float *x_out, cudaStream_t st);

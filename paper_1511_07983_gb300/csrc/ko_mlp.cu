@@ -416,6 +416,34 @@ __global__ void targets_kernel(const int64_t *ms, const int *sid, const double *
     }
 }
 
+// All single-step neighbours of `beam` base orders (rows of stride 24): first
+// the n(n-1)/2 swaps of two positions, then the n(n-1) moves of one kernel to
+// another position (the rest shift by one).  Row r = b * per + q.
+__global__ void neighbours_kernel(const int8_t *__restrict__ base, int beam, int n, int8_t *out)
+{
+    const int swaps = n * (n - 1) / 2, per = swaps + n * (n - 1);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= beam * per) return;
+    const int b = r / per, q = r % per;
+    int8_t p[kMaxK];
+    for (int i = 0; i < n; i++) p[i] = base[b * kMaxK + i];
+    if (q < swaps) {
+        int i = 0, rem = q;
+        while (rem >= n - 1 - i) { rem -= n - 1 - i; i++; }
+        const int j = i + 1 + rem;
+        const int8_t t = p[i]; p[i] = p[j]; p[j] = t;
+    } else {
+        const int m = q - swaps, from = m / (n - 1), k = m % (n - 1);
+        const int to = k < from ? k : k + 1;
+        const int8_t v = p[from];
+        if (from < to) { for (int i = from; i < to; i++) p[i] = p[i + 1]; }
+        else { for (int i = from; i > to; i--) p[i] = p[i - 1]; }
+        p[to] = v;
+    }
+    int8_t *o = out + (size_t)r * kMaxK;
+    for (int i = 0; i < kMaxK; i++) o[i] = i < n ? p[i] : (int8_t)0;
+}
+
 __global__ void random_pick_kernel(int *pick, int B, long long pool, unsigned long long seed)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -554,6 +582,16 @@ cudaError_t ko_mlp_pick(int *pick, int B, long long pool, unsigned long long see
     random_pick_kernel<<<(B + 255) / 256, 256, 0, st>>>(pick, B, pool, seed);
     gather_f32_kernel<<<(B + 255) / 256, 256, 0, st>>>(t_src, pick, B, t_dst);
     ko_count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t ko_mlp_neighbours(const int8_t *base, int beam, int n, int8_t *out, cudaStream_t st)
+{
+    const int per = n * (n - 1) / 2 + n * (n - 1);
+    const int rows = beam * per;
+    if (rows <= 0) return cudaSuccess;
+    neighbours_kernel<<<(rows + 127) / 128, 128, 0, st>>>(base, beam, n, out);
+    ko_count_launch();
     return cudaGetLastError();
 }
 

@@ -31,6 +31,10 @@ constexpr long long kParams = kOffB4 + 1;
 cudaError_t ko_mlp_gemm_relu(const uint16_t *A, int lda, const uint16_t *Bt, int ldb, int M, int N, int K,
                              const float *bias, uint16_t *out, int ldo, uint16_t *out_t, int ldt,
                              cudaStream_t st);
+// tcgen05 forward layer: out = bf16(relu(A Wt^T + bias)), M % 128 == 0,
+// K in {192, 256}, N = 256; *err set to 1 if the MMA completion wait gave up.
+cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
+                            int *err, cudaStream_t st);
 cudaError_t ko_mlp_gemm_f32(const uint16_t *A, int lda, const uint16_t *Bt, int ldb, int M, int N, int K,
                             float *out, int ldo, cudaStream_t st);
 cudaError_t ko_mlp_encode(const int8_t *rows, int row_stride, const int *sid, const int *pick,
@@ -54,5 +58,6 @@ cudaError_t ko_mlp_targets(const int64_t *ms, const int *sid, const double *log2
                            cudaStream_t st);
 cudaError_t ko_mlp_pick(int *pick, int B, long long pool, unsigned long long seed, const float *t_src,
                         float *t_dst, cudaStream_t st);
+cudaError_t ko_mlp_neighbours(const int8_t *base, int beam, int n, int8_t *out, cudaStream_t st);
 cudaError_t ko_mlp_gather_rows(const int8_t *src, int stride, const int *pick, int B, int8_t *dst,
                                cudaStream_t st);

@@ -3,6 +3,7 @@
 // exactly by the run-length simulator.  (The paper has no learned component;
 // this serves the same goal as Algorithm 1 -- a good launch order without
 // trying all N! -- and is judged by the exact simulator.)
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -77,6 +78,8 @@ struct ko_model {
     float *y = nullptr, *t = nullptr, *da = nullptr, *loss = nullptr;
     int *pick = nullptr;
     KoFastState fast{};
+    int tc_forward = 0;        // inference layers on tcgen05 (1) or mma.sync (0)
+    int *tc_err = nullptr;     // device flag: a tcgen05 completion wait gave up
 
     void free_acts()
     {
@@ -90,7 +93,7 @@ struct ko_model {
     ~ko_model()
     {
         free_acts();
-        cudaFree(p); cudaFree(m); cudaFree(v); cudaFree(g); cudaFree(loss);
+        cudaFree(p); cudaFree(m); cudaFree(v); cudaFree(g); cudaFree(loss); cudaFree(tc_err);
         cudaFree(w1t); cudaFree(w2); cudaFree(w2t); cudaFree(w3); cudaFree(w3t); cudaFree(w4b);
         ko_fast_release(&fast);
     }
@@ -136,6 +139,12 @@ ko_status refresh_bf16(ko_model *md, cudaStream_t st)
 ko_status forward(ko_model *md, int B, bool train, cudaStream_t st)
 {
     ko_status s;
+    if (!train && md->tc_forward && B % 128 == 0) {
+        if ((s = cuda_ok(ko_mlp_layer_tc(md->a0, md->w1t, B, kMlpIn, md->p + kOffB1, md->a1, md->tc_err, st)))) return s;
+        if ((s = cuda_ok(ko_mlp_layer_tc(md->a1, md->w2t, B, kHidden, md->p + kOffB2, md->a2, md->tc_err, st)))) return s;
+        if ((s = cuda_ok(ko_mlp_layer_tc(md->a2, md->w3t, B, kHidden, md->p + kOffB3, md->a3, md->tc_err, st)))) return s;
+        return cuda_ok(ko_mlp_out_fwd(md->a3, md->w4b, md->p + kOffB4, B, md->y, st));
+    }
     if ((s = cuda_ok(ko_mlp_gemm_relu(md->a0, kMlpIn, md->w1t, kMlpIn, B, kHidden, kMlpIn, md->p + kOffB1,
                                       md->a1, kHidden, train ? md->a1t : nullptr, B, st))))
         return s;
@@ -220,7 +229,7 @@ ko_model *ko_model_new(uint64_t seed, ko_status *err)
               dalloc(&md->g, kParams) && dalloc(&md->w1t, (size_t)kMlpIn * kHidden) &&
               dalloc(&md->w2, (size_t)kHidden * kHidden) && dalloc(&md->w2t, (size_t)kHidden * kHidden) &&
               dalloc(&md->w3, (size_t)kHidden * kHidden) && dalloc(&md->w3t, (size_t)kHidden * kHidden) &&
-              dalloc(&md->w4b, (size_t)kHidden) && dalloc(&md->loss, 1 << 16);
+              dalloc(&md->w4b, (size_t)kHidden) && dalloc(&md->loss, 1 << 16) && dalloc(&md->tc_err, 1);
     if (!ok) { delete md; *err = KO_ERR_NOMEM; return nullptr; }
     // He-normal initialisation from a counter-based generator (zero biases,
     // zero weights on the padded input features)
@@ -258,6 +267,22 @@ ko_status ko_model_store(const ko_model *md, float *params)
 
 void ko_model_free(ko_model *md) { delete md; }
 
+ko_status ko_model_option(ko_model *md, int key, long long value)
+{
+    if (key != 1 || (value != 0 && value != 1)) return KO_ERR_ARG;
+    md->tc_forward = (int)value;
+    if (cudaMemset(md->tc_err, 0, sizeof(int)) != cudaSuccess) return KO_ERR_CUDA;
+    return KO_OK;
+}
+
+// KO_ERR_TIMEOUT if a tcgen05 layer reported that its completion wait gave up.
+ko_status ko_model_check(ko_model *md)
+{
+    int e = 0;
+    if (cudaMemcpy(&e, md->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return KO_ERR_CUDA;
+    return e ? KO_ERR_TIMEOUT : KO_OK;
+}
+
 // Raw features: forward, and optionally backward (+ Adam when lr > 0).
 ko_status ko_model_raw(ko_model *md, const float *x, const float *t, int B, float *y_out, float *grad_out,
                        float *loss_out, float lr, cudaStream_t st)
@@ -284,7 +309,8 @@ ko_status ko_model_raw(ko_model *md, const float *x, const float *t, int B, floa
     }
     if (y_out && cudaMemcpyAsync(y_out, md->y, sizeof(float) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return KO_ERR_CUDA;
-    return cudaStreamSynchronize(st) == cudaSuccess ? KO_OK : KO_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return KO_ERR_CUDA;
+    return ko_model_check(md);
 }
 
 // ------------------------------------------------------------ set plumbing
@@ -473,6 +499,7 @@ ko_status ko_model_propose_set(ko_model *md, const KoSet &h, long long n_cand, i
         cudaEventRecord(e1, st);
         if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;
     }
+    if (!s) s = ko_model_check(md);
     if (!s) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -489,6 +516,137 @@ ko_status ko_model_propose_set(ko_model *md, const KoSet &h, long long n_cand, i
     if (e1) cudaEventDestroy(e1);
     cudaFree(rows); cudaFree(top_rows); cudaFree(y_all); cudaFree(top_idx); cudaFree(top_ms);
     cudaFree(sel_state); cudaFree(sel_hist); cudaFree(sel_cnt); cudaFree(d_chunk);
+    return s;
+}
+
+// Surrogate-guided local search.  Screening: the network scores n_cand
+// uniform random orders, the top_k are rescored exactly, and the `beam` best
+// exact orders seed the search.  Each round: every swap and every single move
+// of each beam order is scored by the network, the k2 best are rescored
+// exactly, and the beam becomes the `beam` best distinct orders seen so far.
+// Every reported makespan is exact.
+ko_status ko_model_search_set(ko_model *md, const KoSet &h, long long n_cand, int top_k, int rounds, int beam,
+                              uint64_t seed, int32_t *best_order, int64_t *best_makespan, double *gpu_ms,
+                              cudaStream_t st)
+{
+    const int n = h.n;
+    if (n_cand < 1 || top_k < 1 || top_k > n_cand || n_cand > (1ll << 26) || rounds < 0 || rounds > 1024 ||
+        beam < 1 || beam > 64 || n < 2)
+        return KO_ERR_ARG;
+    if (!ko_fast_applicable(h)) return KO_ERR_OVERFLOW;
+    const KoSet *hs[1] = {&h};
+    SetTables tb;
+    ko_status s = build_tables(hs, 1, &tb, st);
+    if (s) return s;
+    const int C = 65536;
+    const int k2 = 256;
+    const long long padded = (n_cand + C - 1) / C * C;
+    const int per = n * (n - 1) / 2 + n * (n - 1);
+    const int nb_rows = beam * per, nb_pad = (nb_rows + 127) / 128 * 128;
+    const int kmax = top_k > k2 ? top_k : k2;
+    int8_t *rows = nullptr, *top_rows = nullptr, *nb = nullptr, *base = nullptr;
+    float *y_all = nullptr;
+    int *top_idx = nullptr;
+    int64_t *top_ms = nullptr;
+    uint32_t *sel_state = nullptr;
+    unsigned int *sel_hist = nullptr, *sel_cnt = nullptr;
+    KoChunk *d_chunk = nullptr;
+    if (!dalloc(&rows, (size_t)padded * kMaxK) || !dalloc(&y_all, (size_t)std::max<long long>(n_cand, nb_pad)) ||
+        !dalloc(&top_idx, kmax) || !dalloc(&top_rows, (size_t)kmax * kMaxK) || !dalloc(&top_ms, kmax) ||
+        !dalloc(&nb, (size_t)nb_pad * kMaxK) || !dalloc(&base, (size_t)beam * kMaxK) || !dalloc(&sel_state, 2) ||
+        !dalloc(&sel_hist, 256) || !dalloc(&sel_cnt, 2) || !dalloc(&d_chunk, 1))
+        s = KO_ERR_NOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct Cand {
+        int64_t ms;
+        std::vector<int8_t> row;
+    };
+    std::vector<Cand> pool;
+    // exact makespans of `cnt` device rows -> pool
+    auto collect = [&](int cnt) -> ko_status {
+        std::vector<int64_t> hm(cnt);
+        std::vector<int8_t> hr((size_t)cnt * kMaxK);
+        if (cudaMemcpyAsync(hm.data(), top_ms, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hr.data(), top_rows, hr.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return KO_ERR_CUDA;
+        for (int i = 0; i < cnt; i++)
+            if (hm[i] >= 0) pool.push_back(Cand{hm[i], std::vector<int8_t>(hr.begin() + (size_t)i * kMaxK, hr.begin() + (size_t)(i + 1) * kMaxK)});
+        std::stable_sort(pool.begin(), pool.end(), [](const Cand &a, const Cand &b) { return a.ms < b.ms; });
+        std::vector<Cand> kept;
+        for (const Cand &c : pool) {
+            bool dup = false;
+            for (const Cand &k : kept) dup = dup || k.row == c.row;
+            if (!dup) kept.push_back(c);
+            if ((int)kept.size() == beam) break;
+        }
+        pool.swap(kept);
+        return KO_OK;
+    };
+    if (!s) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        s = ensure_acts(md, C);
+    }
+    if (!s) {
+        cudaEventRecord(e0, st);
+        // screening
+        if (cudaMemsetAsync(rows, 0, (size_t)padded * kMaxK, st) != cudaSuccess ||
+            cudaMemsetAsync(nb, 0, (size_t)nb_pad * kMaxK, st) != cudaSuccess)
+            s = KO_ERR_CUDA;
+        if (!s) s = cuda_ok(ko_mlp_random_orders(rows, kMaxK, n_cand, n, mix64(seed ^ 0xC0FFEEull), st));
+        for (long long off = 0; off < n_cand && !s; off += C) {
+            const long long c = n_cand - off < C ? n_cand - off : C;
+            if ((s = cuda_ok(ko_mlp_encode(rows + (size_t)off * kMaxK, kMaxK, nullptr, nullptr, tb.set_n, tb.kfeat,
+                                           tb.gfeat, C, md->a0, nullptr, st))))
+                break;
+            if ((s = forward(md, C, false, st))) break;
+            if (cudaMemcpyAsync(y_all + off, md->y, sizeof(float) * c, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                s = KO_ERR_CUDA;
+        }
+        if (!s) s = cuda_ok(ko_mlp_topk(y_all, n_cand, top_k, sel_state, sel_hist, sel_cnt, top_idx, st));
+        if (!s) s = cuda_ok(ko_mlp_gather_rows(rows, kMaxK, top_idx, top_k, top_rows, st));
+        if (!s) s = exact_rows(&md->fast, tb.sets, h, 0, top_rows, top_k, top_ms, d_chunk, st);
+        if (!s) s = collect(top_k);
+        // local search rounds
+        for (int r = 0; r < rounds && !s && !pool.empty(); r++) {
+            const int nbase = (int)pool.size();
+            std::vector<int8_t> hb((size_t)nbase * kMaxK);
+            for (int i = 0; i < nbase; i++) std::memcpy(&hb[(size_t)i * kMaxK], pool[i].row.data(), kMaxK);
+            if (cudaMemcpyAsync(base, hb.data(), hb.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) { s = KO_ERR_CUDA; break; }
+            if ((s = cuda_ok(ko_mlp_neighbours(base, nbase, n, nb, st)))) break;
+            const int q = nbase * per, qpad = (q + 127) / 128 * 128;
+            for (int off = 0; off < qpad && !s; off += C) {
+                const int c = qpad - off < C ? qpad - off : C;
+                if ((s = cuda_ok(ko_mlp_encode(nb + (size_t)off * kMaxK, kMaxK, nullptr, nullptr, tb.set_n, tb.kfeat,
+                                               tb.gfeat, c, md->a0, nullptr, st))))
+                    break;
+                if ((s = forward(md, c, false, st))) break;
+                if (cudaMemcpyAsync(y_all + off, md->y, sizeof(float) * c, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    s = KO_ERR_CUDA;
+            }
+            const int kk = q < k2 ? q : k2;
+            if (!s) s = cuda_ok(ko_mlp_topk(y_all, q, kk, sel_state, sel_hist, sel_cnt, top_idx, st));
+            if (!s) s = cuda_ok(ko_mlp_gather_rows(nb, kMaxK, top_idx, kk, top_rows, st));
+            if (!s) s = exact_rows(&md->fast, tb.sets, h, 0, top_rows, kk, top_ms, d_chunk, st);
+            if (!s) s = collect(kk);
+        }
+        cudaEventRecord(e1, st);
+        if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;
+    }
+    if (!s) s = ko_model_check(md);
+    if (!s && pool.empty()) s = KO_ERR_STATE;
+    if (!s) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (gpu_ms) *gpu_ms = ms;
+        *best_makespan = pool[0].ms;
+        for (int i = 0; i < n; i++) best_order[i] = pool[0].row[i];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rows); cudaFree(top_rows); cudaFree(nb); cudaFree(base); cudaFree(y_all); cudaFree(top_idx);
+    cudaFree(top_ms); cudaFree(sel_state); cudaFree(sel_hist); cudaFree(sel_cnt); cudaFree(d_chunk);
     return s;
 }
 

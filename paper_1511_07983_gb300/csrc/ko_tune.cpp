@@ -95,20 +95,33 @@ void write_cache(const char *path, const std::map<std::string, Choice> &m)
 
 }  // namespace
 
-// Times one candidate on the calibration slice; returns orders per second
-// (0 on failure).  d_set / d_chunk / d_acc are device scratch of the caller.
-double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
-                       KoAccum *d_acc, int lanes, int levels, cudaStream_t st)
+// Calibration slice of a candidate depth: about 4M orders, but at least 20k
+// work items (enough to fill the GPU) unless the space is smaller; 0 when
+// such a slice would exceed 40M orders (too deep to be worth timing).
+long long ko_tune_items(int n, int levels)
 {
-    const int n = h.n;
     int d0 = n - 1 - levels;
     if (d0 < 0) d0 = 0;
     const long long items_all = kFact[n] / kFact[n - d0];
     const long long span = kFact[n - d0];
-    // enough items to fill the GPU several times over, at most the whole space
-    long long items = 60000;
-    if (items * span < 2000000) items = (2000000 + span - 1) / span;
+    long long items = (4000000 + span - 1) / span;
+    if (items < 20000) items = 20000;
     if (items > items_all) items = items_all;
+    if (items * span > 40000000 && items < items_all) return 0;
+    return items;
+}
+
+// Times one candidate on its calibration slice; returns orders per second
+// (0 on failure).  d_set / d_chunk / d_acc are device scratch of the caller.
+double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
+                       KoAccum *d_acc, int lanes, int levels, int reps, cudaStream_t st)
+{
+    const int n = h.n;
+    int d0 = n - 1 - levels;
+    if (d0 < 0) d0 = 0;
+    const long long span = kFact[n - d0];
+    const long long items = ko_tune_items(n, levels);
+    if (items <= 0) return 0.0;
     KoChunk c{};
     c.count = items;
     c.d0 = d0;
@@ -127,7 +140,7 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double rate = 0.0;
-    for (int rep = 0; rep < 2; rep++) {  // first run warms up
+    for (int rep = 0; rep < reps; rep++) {
         if (ko_launch_accum_reset(d_acc, 1, st) != cudaSuccess) break;
         cudaEventRecord(e0, st);
         if (ko_fast_launch(fs, w, ko_slab_bytes(h.S, h.Bk), st) != KO_OK) break;
@@ -160,14 +173,13 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChu
     }
     Choice best;
     best.rate = -1.0;
-    const int max_levels = h.n - 1 < 6 ? h.n - 1 : 6;
+    const int max_levels = h.n - 1 < 5 ? h.n - 1 : 5;
+    bool warmed = false;
     for (int lanes : {32, 16}) {
         for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
-            // work items must stay plentiful: at least ~16k unless the space is small
-            const int d0 = h.n - 1 - levels > 0 ? h.n - 1 - levels : 0;
-            const long long items = kFact[h.n] / kFact[h.n - d0];
-            if (items < 16384 && kFact[h.n] > 16384LL * 24 && levels > 1) continue;
-            const double r = ko_tune_measure(fs, h, d_set, d_chunk, d_acc, lanes, levels, st);
+            if (ko_tune_items(h.n, levels) <= 0) continue;
+            const double r = ko_tune_measure(fs, h, d_set, d_chunk, d_acc, lanes, levels, warmed ? 1 : 2, st);
+            warmed = true;
             if (r > best.rate) {
                 best.rate = r;
                 best.lanes = lanes;

@@ -86,9 +86,14 @@ _SIGNATURES = {
     "ko_surrogate_propose": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "ko_surrogate_search": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_void_p]),
     "ko_random_search": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
+    "ko_model_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -325,6 +330,10 @@ class Model:
         if not self.m:
             raise KoError(lib().ko_last_error(), "ko_model_create")
 
+    def set_tc(self, on: bool):
+        """Inference layers on tcgen05 (True) or warp-level mma.sync (False)."""
+        _check(lib().ko_model_set_option(self.m, 1, int(bool(on))), "ko_model_set_option")
+
     def get_params(self):
         out = np.empty(KO_MODEL_PARAMS, dtype=np.float32)
         _check(lib().ko_model_get_params(self.m, _ptr(out)), "ko_model_get_params")
@@ -371,6 +380,14 @@ class Model:
         t = ctypes.c_double()
         _check(lib().ko_surrogate_propose(self.m, g.h, n_cand, top_k, seed, _ptr(order), ctypes.byref(ms),
                                           ctypes.byref(t), _stream(stream)), "ko_surrogate_propose")
+        return order[:g.n], ms.value, t.value
+
+    def search(self, g, n_cand=1 << 20, top_k=1024, rounds=8, beam=8, seed=0, stream=None):
+        order = np.zeros(max(g.n, 1), dtype=np.int32)
+        ms = ctypes.c_int64()
+        t = ctypes.c_double()
+        _check(lib().ko_surrogate_search(self.m, g.h, n_cand, top_k, rounds, beam, seed, _ptr(order),
+                                         ctypes.byref(ms), ctypes.byref(t), _stream(stream)), "ko_surrogate_search")
         return order[:g.n], ms.value, t.value
 
     def close(self):

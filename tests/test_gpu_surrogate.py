@@ -129,3 +129,14 @@ def test_propose_and_random_search_are_exact(ko):
         ro, rms, _ = ko.ko_random_search(g, 5000, seed=4)
         assert sorted(ro.tolist()) == list(range(s.n))
         assert rms == oracle.makespan(s.gpu, s.kernels, ro.tolist())
+
+
+def test_guided_search_is_exact_and_not_worse_than_screening(ko):
+    s = synth.gen_set("large", 5)
+    m = ko.Model(seed=2)
+    with ko.Gpu.from_set(s) as g:
+        _, screened, _ = m.search(g, n_cand=70000, top_k=256, rounds=0, beam=4, seed=3)
+        order, ms, t_ms = m.search(g, n_cand=70000, top_k=256, rounds=3, beam=4, seed=3)
+    assert sorted(order.tolist()) == list(range(s.n)) and t_ms > 0
+    assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
+    assert ms <= screened      # the beam always keeps the screening's best
