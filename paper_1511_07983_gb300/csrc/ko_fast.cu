@@ -93,6 +93,24 @@ struct Run {
     uint32_t ge[G];
 };
 
+// Register-array access by a run-time slot index without local memory: a
+// chain of selects (read) or predicated moves (write) over the unrolled slots.
+template <int G>
+__device__ __forceinline__ uint32_t slot_get(const uint32_t (&a)[G], int g)
+{
+    uint32_t v = a[0];
+#pragma unroll
+    for (int i = 1; i < G; i++) v = g == i ? a[i] : v;
+    return v;
+}
+template <int G>
+__device__ __forceinline__ void slot_set(uint32_t (&a)[G], int g, uint32_t v)
+{
+#pragma unroll
+    for (int i = 0; i < G; i++)
+        if (g == i) a[i] = v;
+}
+
 template <int LANES, int G>
 struct Sim {
     static constexpr int kG = G;
@@ -210,42 +228,51 @@ struct Sim {
         const int L = lo;
         const int full = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * min(cap, L - 1)));
         const int rem = left - full;  // 1 .. number of SMs with cap >= L
-        // the run holding p is cut at p when its SMs are eligible, so that the
-        // cyclic order from p is a rotation of whole runs
+        // Two cuts, one split site: phase 0 cuts the run holding p at p when its
+        // SMs are eligible (so the cyclic order from p is a rotation of whole
+        // runs); phase 1 cuts the run where the last partial sweep ends.
         int jp = __ffs(seg_ballot(sg, run.cnt > 0 && run.beg <= p && p < run.beg + run.cnt)) - 1;
-        {
-            const int beg_jp = shfl(run.beg, jp), cap_jp = shfl(cap, jp);
-            if (beg_jp < p && cap_jp >= L) {
-                int dummy = 0;
-                split(jp, p - beg_jp, cap, dummy);
-                if (fail) return;
-                jp++;
-            }
-        }
-        const int e = (run.cnt > 0 && cap >= L) ? run.cnt : 0;
-        int incl = e;
+        int plus = 0, star = 0, x = 0, beg_star = 0;
+#pragma unroll 1
+        for (int phase = 0; phase < 2; phase++) {
+            int cut_lane, cut_at;
+            bool need;
+            if (phase == 0) {
+                const int beg_jp = shfl(run.beg, jp), cap_jp = shfl(cap, jp);
+                need = beg_jp < p && cap_jp >= L;
+                cut_lane = jp;
+                cut_at = p - beg_jp;
+            } else {
+                const int e = (run.cnt > 0 && cap >= L) ? run.cnt : 0;
+                int incl = e;
 #pragma unroll
-        for (int o = 1; o < LANES; o <<= 1) {
-            const int v = __shfl_up_sync(sg.mask, incl, o, LANES);
-            if (sg.lane >= o) incl += v;
-        }
-        const int excl = incl - e;
-        const int E = shfl(incl, LANES - 1);
-        const int excl_jp = shfl(excl, jp);
-        const int rot = sg.lane >= jp ? excl - excl_jp : E - excl_jp + excl;
-        const int star = __ffs(seg_ballot(sg, e > 0 && rot < rem && rem <= rot + e)) - 1;
-        const int x = rem - shfl(rot, star);
-        const int cnt_star = shfl(run.cnt, star);
-        const int beg_star = shfl(run.beg, star);
-        // rotated position of each lane relative to jp
-        const int rl = sg.lane >= jp ? sg.lane - jp : sg.lane - jp + nruns;
-        const int rs = star >= jp ? star - jp : star - jp + nruns;
-        int plus = (e > 0 && rl < rs) ? 1 : 0;
-        if (sg.lane == star) plus = 1;
-        if (x < cnt_star) {
-            split(star, x, cap, plus);
-            if (fail) return;
-            if (sg.lane == star + 1) plus = 0;
+                for (int o = 1; o < LANES; o <<= 1) {
+                    const int v = __shfl_up_sync(sg.mask, incl, o, LANES);
+                    if (sg.lane >= o) incl += v;
+                }
+                const int excl = incl - e;
+                const int E = shfl(incl, LANES - 1);
+                const int excl_jp = shfl(excl, jp);
+                const int rot = sg.lane >= jp ? excl - excl_jp : E - excl_jp + excl;
+                star = __ffs(seg_ballot(sg, e > 0 && rot < rem && rem <= rot + e)) - 1;
+                x = rem - shfl(rot, star);
+                const int cnt_star = shfl(run.cnt, star);
+                beg_star = shfl(run.beg, star);
+                // rotated position of each lane relative to jp
+                const int rl = sg.lane >= jp ? sg.lane - jp : sg.lane - jp + nruns;
+                const int rs = star >= jp ? star - jp : star - jp + nruns;
+                plus = (e > 0 && rl < rs) ? 1 : 0;
+                if (sg.lane == star) plus = 1;
+                need = x < cnt_star;
+                cut_lane = star;
+                cut_at = x;
+            }
+            if (need) {
+                split(cut_lane, cut_at, cap, plus);
+                if (fail) return;
+                if (phase == 0) jp++;
+                else if (sg.lane == star + 1) plus = 0;
+            }
         }
         p = beg_star + x;
         if (p >= K.S) p -= K.S;
@@ -267,17 +294,21 @@ struct Sim {
         return (uint32_t)(dc > dm ? dc : dm);
     }
 
-    // Fix the durations of the groups started in the open burst.
+    // Fix the durations of the groups started in the open burst (one body,
+    // looped over the set bits of each lane's pending mask).
     __device__ void close_burst(const SetConst &K)
     {
         const uint32_t t32 = (uint32_t)t;
+        uint32_t pend = 0;
 #pragma unroll
-        for (int g = 0; g < kG; g++) {
-            if (__any_sync(sg.mask, (run.gk[g] & kPend) != 0)) {
-                if (run.gk[g] & kPend) {
-                    run.ge[g] = t32 + duration(K, run.gk[g] & 31u);
-                    run.gk[g] &= ~kPend;
-                }
+        for (int g = 0; g < kG; g++) pend |= ((run.gk[g] & kPend) ? 1u : 0u) << g;
+        while (__any_sync(sg.mask, pend != 0)) {
+            if (pend) {
+                const int g = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const uint32_t w = slot_get(run.gk, g);
+                slot_set(run.ge, g, t32 + duration(K, w & 31u));
+                slot_set(run.gk, g, w & ~kPend);
             }
         }
     }
@@ -294,17 +325,19 @@ struct Sim {
         if (dmin == 0xffffffffu) { fail = 1; return; }
         t += dmin;
         const uint32_t now = t32 + dmin;
+        uint32_t rel = 0;
 #pragma unroll
-        for (int g = 0; g < kG; g++) {
-            const bool rel = run.gk[g] != 0 && run.ge[g] == now;
-            if (__any_sync(sg.mask, rel)) {
-                if (rel) {
-                    const int kid = run.gk[g] & 31u;
-                    const int q = (run.gk[g] >> 8) & 63u;
-                    run.ur -= q * K.r[kid]; run.us -= q * K.s[kid]; run.uw -= q * K.w[kid];
-                    run.ub -= q; run.sc -= q * K.c[kid]; run.sm -= q * K.m[kid];
-                    run.gk[g] = 0;
-                }
+        for (int g = 0; g < kG; g++) rel |= (run.gk[g] != 0 && run.ge[g] == now ? 1u : 0u) << g;
+        while (__any_sync(sg.mask, rel != 0)) {
+            if (rel) {
+                const int g = __ffs(rel) - 1;
+                rel &= rel - 1;
+                const uint32_t w = slot_get(run.gk, g);
+                const int kid = w & 31u;
+                const int q = (w >> 8) & 63u;
+                run.ur -= q * K.r[kid]; run.us -= q * K.s[kid]; run.uw -= q * K.w[kid];
+                run.ub -= q; run.sc -= q * K.c[kid]; run.sm -= q * K.m[kid];
+                slot_set(run.gk, g, 0u);
             }
         }
     }

@@ -14,7 +14,8 @@
 //    time with tcgen05.ld.32x32b.x32, adds the bias, applies ReLU, rounds to
 //    BF16 and stores.
 // Shared memory (192 KB at K = 256) keeps one CTA per SM, so the 256-column
-// TMEM allocation never waits for another CTA.
+// TMEM allocation never waits for another CTA.  The grid is persistent (one
+// CTA per SM): weights are loaded once per CTA, row tiles stream through.
 #include <cstdint>
 
 #include "ko_mlp.h"
@@ -48,16 +49,25 @@ __host__ __device__ constexpr uint32_t instr_desc(int m, int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+__device__ __forceinline__ void cp_async16_tc(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr(dst)), "l"(src));
+}
+
+// Persistent: one CTA per SM loads the weights once, then walks row tiles
+// (tile, tile + gridDim.x, ...).  Operand copies use cp.async, made visible
+// to the tensor core's async proxy before each MMA batch; the mbarrier phase
+// alternates per tile.
 __global__ void __launch_bounds__(128, 1)
-tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt, int K,
+tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt, int K, int tiles,
                 const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * kTileM;
     const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    const int kc = K / 8;
     uint8_t *sa = smem;                              // 128 x K
     uint8_t *sb = smem + (size_t)kTileM * K * 2;     // 256 x K
 
@@ -69,81 +79,89 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
-    // operands into the core-matrix layout: 16-byte chunk (row r, k-chunk c)
-    // goes to (r / 8) * SBO + c * 128 + (r % 8) * 16
-    const int kc = K / 8;
-    for (int i = tid; i < kTileM * kc; i += blockDim.x) {
-        const int r = i / kc, c = i % kc;
-        const uint4 v = *(const uint4 *)(A + (size_t)(m0 + r) * K + c * 8);
-        *(uint4 *)(sa + (r >> 3) * sbo + c * 128 + (r & 7) * 16) = v;
-    }
+    // weights once: 16-byte chunk (row r, k-chunk c) -> (r / 8) * SBO + c * 128 + (r % 8) * 16
     for (int i = tid; i < kTileN * kc; i += blockDim.x) {
         const int r = i / kc, c = i % kc;
-        const uint4 v = *(const uint4 *)(Wt + (size_t)r * K + c * 8);
-        *(uint4 *)(sb + (r >> 3) * sbo + c * 128 + (r & 7) * 16) = v;
+        cp_async16_tc(sb + (r >> 3) * sbo + c * 128 + (r & 7) * 16, Wt + (size_t)r * K + c * 8);
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = tmem_base;
-
-    if (tid == 0) {
-        const uint32_t idesc = instr_desc(kTileM, kTileN);
-        for (int k = 0; k < K / 16; k++) {
-            // a 16-wide K step covers two core matrices along K
-            const uint64_t ad = smem_desc(saddr(sa) + (uint32_t)k * 256u, 128u, sbo);
-            const uint64_t bd = smem_desc(saddr(sb) + (uint32_t)k * 256u, 128u, sbo);
-            const uint32_t acc = k > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    const uint32_t idesc = instr_desc(kTileM, kTileN);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, phase ^= 1u) {
+        const int m0 = tile * kTileM;
+        for (int i = tid; i < kTileM * kc; i += blockDim.x) {
+            const int r = i / kc, c = i % kc;
+            cp_async16_tc(sa + (r >> 3) * sbo + c * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * K + c * 8);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            saddr(&mbar)));
-    }
-    // bounded wait for the MMAs (phase 0)
-    uint32_t done = 0;
-    for (uint32_t spin = 0; spin < kSpinLimit && !done; spin++) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(saddr(&mbar)));
-    }
-    if (!done) {
-        if (lane == 0) atomicExch(err, 1);
-    } else {
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_all;\n" ::);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kTileN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                  "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                  "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-            uint32_t packed[16];
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.0f);
-                const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.0f);
-                packed[j] = (uint32_t)bf16_bits_tc(x0) | ((uint32_t)bf16_bits_tc(x1) << 16);
+        if (tid == 0) {
+            for (int k = 0; k < K / 16; k++) {
+                // a 16-wide K step covers two core matrices along K
+                const uint64_t ad = smem_desc(saddr(sa) + (uint32_t)k * 256u, 128u, sbo);
+                const uint64_t bd = smem_desc(saddr(sb) + (uint32_t)k * 256u, 128u, sbo);
+                const uint32_t acc = k > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
-            uint4 *dst = (uint4 *)(out + (size_t)row * kTileN + c0);
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                saddr(&mbar)));
         }
+        uint32_t done = 0;
+        for (uint32_t spin = 0; spin < kSpinLimit && !done; spin++) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(saddr(&mbar)), "r"(phase));
+        }
+        if (!done) {
+            if (lane == 0) atomicExch(err, 1);
+            ok = false;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const int row = m0 + warp * 32 + lane;
+            for (int c0 = 0; c0 < kTileN; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                uint32_t packed[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.0f);
+                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.0f);
+                    packed[j] = (uint32_t)bf16_bits_tc(x0) | ((uint32_t)bf16_bits_tc(x1) << 16);
+                }
+                uint4 *dst = (uint4 *)(out + (size_t)row * kTileN + c0);
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+            }
+        }
+        // the next tile overwrites the A tile and the accumulator
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
 }
 
@@ -156,7 +174,12 @@ cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K,
     const size_t smem = (size_t)(kTileM + kTileN) * K * 2;
     cudaError_t e = cudaFuncSetAttribute(tc_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tc_layer_kernel<<<M / kTileM, 128, smem, st>>>(A, Wt, K, bias, out, err);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = M / kTileM;
+    const int grid = tiles < sms ? tiles : sms;
+    tc_layer_kernel<<<grid, 128, smem, st>>>(A, Wt, K, tiles, bias, out, err);
     ko_count_launch();
     return cudaGetLastError();
 }

@@ -140,3 +140,21 @@ def test_guided_search_is_exact_and_not_worse_than_screening(ko):
     assert sorted(order.tolist()) == list(range(s.n)) and t_ms > 0
     assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
     assert ms <= screened      # the beam always keeps the screening's best
+
+
+def test_tcgen05_forward_matches_mma_and_oracle(ko):
+    p = _params(11)
+    x = _features(12, 1024)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    m.set_tc(False)
+    y_mma = m.predict(x)
+    m.set_tc(True)
+    y_tc = m.predict(x)
+    assert np.allclose(y_tc, y_mma, rtol=1e-5, atol=1e-5)
+    want, _ = mlp.forward(p, x)
+    assert np.abs(y_tc - want).max() <= 2e-2 * max(1.0, np.abs(want).max())
+    s = synth.gen_set("large", 4)
+    with ko.Gpu.from_set(s) as g:
+        order, ms, _ = m.search(g, n_cand=65536, top_k=128, rounds=2, beam=4, seed=1)
+    assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
