@@ -305,9 +305,10 @@ ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *
                            int64_t *best_makespan, double *gpu_ms, void *stream);
 
 /* Model options.  KO_MODEL_OPT_TC: tensor-core path of the inference
- * forward (ko_model_predict, ko_surrogate_propose) -- 0 = warp-level
- * mma.sync BF16 GEMMs (default), 1 = tcgen05 MMAs with TMEM accumulators
- * (batches padded to multiples of 128).  A tcgen05 completion wait that
+ * forward (ko_model_predict, ko_surrogate_propose, ko_surrogate_search) --
+ * 0 = warp-level mma.sync BF16 GEMMs, 1 = tcgen05 MMAs with TMEM
+ * accumulators (default; used for batches that are multiples of 128, the
+ * others fall back to mma.sync).  Both give the same bits.  A tcgen05 completion wait that
  * gives up makes the next call return KO_ERR_TIMEOUT.  Training always uses
  * mma.sync.  KO_ERR_ARG for an unknown key or value. */
 #define KO_MODEL_OPT_TC 1

@@ -78,7 +78,7 @@ struct ko_model {
     float *y = nullptr, *t = nullptr, *da = nullptr, *loss = nullptr;
     int *pick = nullptr;
     KoFastState fast{};
-    int tc_forward = 0;        // inference layers on tcgen05 (1) or mma.sync (0)
+    int tc_forward = 1;        // inference layers on tcgen05 (1) or mma.sync (0)
     int *tc_err = nullptr;     // device flag: a tcgen05 completion wait gave up
 
     void free_acts()
