@@ -40,7 +40,10 @@ constexpr uint32_t kValid = 1u << 16;       // slot holds a group
 // group word: kernel id (bits 0-4) | blocks per SM (bits 8-13) | kPend | kValid
 
 constexpr int kMaxLevels = 6;               // saved DFS levels per segment
-__host__ __device__ constexpr int state_words(int G) { return 8 + 2 * G; }  // per-lane words saved per level
+// Per-lane words saved per DFS level: range (beg | cnt << 16), registers,
+// shared memory, warps | blocks << 25, SumC, SumM, G/2 words of two 13-bit
+// group descriptors, G end times.
+__host__ __device__ constexpr int state_words(int G) { return 6 + G / 2 + G; }
 constexpr int kThreads = 128;
 
 __constant__ unsigned long long c_fact[21] = {
@@ -371,20 +374,33 @@ struct Sim {
 
     // Save / restore the node state; only the first SAVE lanes are stored, so
     // a node with more runs than that abandons the work item.
+    // 13-bit form of a group word: kernel (5) | blocks per SM (6) | pending | valid
+    __device__ __forceinline__ static uint32_t pack13(uint32_t w)
+    {
+        return (w & 31u) | (((w >> 8) & 63u) << 5) | (((w >> 15) & 1u) << 11) | (((w >> 16) & 1u) << 12);
+    }
+    __device__ __forceinline__ static uint32_t unpack13(uint32_t v)
+    {
+        return (v & 31u) | (((v >> 5) & 63u) << 8) | (((v >> 11) & 1u) << 15) | (((v >> 12) & 1u) << 16);
+    }
+
     template <int SAVE>
     __device__ void save(int *slot)
     {
         if (nruns > SAVE) { fail = 1; return; }
         if (sg.lane < SAVE) {
             int *q = slot + sg.lane;
-            q[0 * SAVE] = run.beg; q[1 * SAVE] = run.cnt; q[2 * SAVE] = run.ur;
-            q[3 * SAVE] = run.us; q[4 * SAVE] = run.uw; q[5 * SAVE] = run.ub;
-            q[6 * SAVE] = run.sc; q[7 * SAVE] = run.sm;
+            q[0 * SAVE] = (int)((uint32_t)run.beg | ((uint32_t)run.cnt << 16));
+            q[1 * SAVE] = run.ur;
+            q[2 * SAVE] = run.us;
+            q[3 * SAVE] = (int)((uint32_t)run.uw | ((uint32_t)run.ub << 25));
+            q[4 * SAVE] = run.sc;
+            q[5 * SAVE] = run.sm;
 #pragma unroll
-            for (int g = 0; g < kG; g++) {
-                q[(8 + g) * SAVE] = (int)run.gk[g];
-                q[(8 + kG + g) * SAVE] = (int)run.ge[g];
-            }
+            for (int g = 0; g < kG; g += 2)
+                q[(6 + g / 2) * SAVE] = (int)(pack13(run.gk[g]) | (pack13(run.gk[g + 1]) << 16));
+#pragma unroll
+            for (int g = 0; g < kG; g++) q[(6 + kG / 2 + g) * SAVE] = (int)run.ge[g];
         }
         if (sg.lane == 0) {
             int *u = slot + kStateWords * SAVE;
@@ -398,14 +414,23 @@ struct Sim {
     {
         if (sg.lane < SAVE) {
             const int *q = slot + sg.lane;
-            run.beg = q[0 * SAVE]; run.cnt = q[1 * SAVE]; run.ur = q[2 * SAVE];
-            run.us = q[3 * SAVE]; run.uw = q[4 * SAVE]; run.ub = q[5 * SAVE];
-            run.sc = q[6 * SAVE]; run.sm = q[7 * SAVE];
+            const uint32_t r0 = (uint32_t)q[0 * SAVE], r3 = (uint32_t)q[3 * SAVE];
+            run.beg = (int)(r0 & 0xffffu);
+            run.cnt = (int)(r0 >> 16);
+            run.ur = q[1 * SAVE];
+            run.us = q[2 * SAVE];
+            run.uw = (int)(r3 & 0x1ffffffu);
+            run.ub = (int)(r3 >> 25);
+            run.sc = q[4 * SAVE];
+            run.sm = q[5 * SAVE];
 #pragma unroll
-            for (int g = 0; g < kG; g++) {
-                run.gk[g] = (uint32_t)q[(8 + g) * SAVE];
-                run.ge[g] = (uint32_t)q[(8 + kG + g) * SAVE];
+            for (int g = 0; g < kG; g += 2) {
+                const uint32_t v = (uint32_t)q[(6 + g / 2) * SAVE];
+                run.gk[g] = unpack13(v & 0xffffu);
+                run.gk[g + 1] = unpack13(v >> 16);
             }
+#pragma unroll
+            for (int g = 0; g < kG; g++) run.ge[g] = (uint32_t)q[(6 + kG / 2 + g) * SAVE];
         } else {
             run.beg = 0; run.cnt = 0; run.ur = run.us = run.uw = run.ub = run.sc = run.sm = 0;
 #pragma unroll

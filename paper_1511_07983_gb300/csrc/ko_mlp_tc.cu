@@ -57,7 +57,8 @@ __device__ __forceinline__ void cp_async16_tc(void *dst, const void *src)
 // Persistent: one CTA per SM loads the weights once, then walks row tiles
 // (tile, tile + gridDim.x, ...).  Operand copies use cp.async, made visible
 // to the tensor core's async proxy before each MMA batch; the mbarrier phase
-// alternates per tile.
+// alternates per tile.  The next tile's A operand is requested as soon as the
+// current MMAs complete, so its load overlaps the epilogue.
 __global__ void __launch_bounds__(128, 1)
 tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt, int K, int tiles,
                 const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
@@ -90,15 +91,21 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = instr_desc(kTileM, kTileN);
-    bool ok = true;
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, phase ^= 1u) {
+    // A tile (row tile `tile`) into shared memory with cp.async
+    auto load_a = [&](int tile) {
         const int m0 = tile * kTileM;
         for (int i = tid; i < kTileM * kc; i += blockDim.x) {
             const int r = i / kc, c = i % kc;
             cp_async16_tc(sa + (r >> 3) * sbo + c * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * K + c * 8);
         }
         asm volatile("cp.async.commit_group;\n" ::);
+    };
+    bool ok = true;
+    uint32_t phase = 0;
+    if (blockIdx.x < tiles) load_a(blockIdx.x);
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, phase ^= 1u) {
+        const int m0 = tile * kTileM;
+        // operands of this tile have landed: make them visible to the tensor core
         asm volatile("cp.async.wait_all;\n" ::);
         asm volatile("fence.proxy.async.shared::cta;\n" ::);
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -130,6 +137,8 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
             ok = false;
         } else {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            // the MMAs have read the A tile: start loading the next one under the epilogue
+            if (tile + (int)gridDim.x < tiles) load_a(tile + gridDim.x);
             const int row = m0 + warp * 32 + lane;
             for (int c0 = 0; c0 < kTileN; c0 += 32) {
                 uint32_t v[32];
@@ -157,11 +166,12 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
                     dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
             }
         }
-        // the next tile overwrites the A tile and the accumulator
+        // every warp has drained the accumulator before the next tile's MMAs overwrite it
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     }
+    asm volatile("cp.async.wait_all;\n" ::);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
 }
 
