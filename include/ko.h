@@ -155,6 +155,10 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
  *                       first, saving `levels` states; 0..6 (default 4)
  *   KO_OPT_SIMPLE_ONLY  1 = use only the simple one-thread-per-order
  *                       simulator, 0 = run-length simulator where it applies
+ *   KO_OPT_STACK_GLOBAL 1 = keep saved DFS node states in a global-memory
+ *                       slab (cached in L2/L1) instead of shared memory,
+ *                       which frees shared memory for occupancy and L1 for
+ *                       register spills (default 1); 0 = shared memory
  *   KO_OPT_RUN_LIMIT    most runs of distinct SM states one simulation may
  *                       hold before its work item moves to the simple
  *                       simulator, 1..32 (default 32; small values exercise
@@ -165,6 +169,7 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 #define KO_OPT_LEVELS 2
 #define KO_OPT_SIMPLE_ONLY 3
 #define KO_OPT_RUN_LIMIT 4
+#define KO_OPT_STACK_GLOBAL 5
 ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 
 /* Current value of a tuning knob (KO_OPT_*), or KO_ERR_ARG. */

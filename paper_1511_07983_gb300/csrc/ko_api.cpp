@@ -555,6 +555,10 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
         if (value < 1 || value > 32) return fail(KO_ERR_ARG);
         g->fast.run_limit = (int)value;
         break;
+    case KO_OPT_STACK_GLOBAL:
+        if (value != 0 && value != 1) return fail(KO_ERR_ARG);
+        g->fast.stack_global = (int)value;
+        break;
     default:
         return fail(KO_ERR_ARG);
     }
@@ -569,6 +573,7 @@ int64_t ko_get_option(const ko_gpu *g, int32_t key)
     case KO_OPT_LEVELS: return g->fast.levels;
     case KO_OPT_SIMPLE_ONLY: return g->fast.disabled ? 1 : 0;
     case KO_OPT_RUN_LIMIT: return g->fast.run_limit;
+    case KO_OPT_STACK_GLOBAL: return g->fast.stack_global;
     default: return fail(KO_ERR_ARG);
     }
 }

@@ -532,7 +532,14 @@ fast_kernel(KoWork a)
     sim.run_limit = a.run_limit < LANES ? a.run_limit : LANES;
     sim.sg.mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
     const int level_words = kStateWords * SAVE + 4;
+    // node states: per segment, in shared memory or in a global slab
     int *stack = stack_mem + seg * a.levels * level_words;
+    if (a.gstack) {
+        const long long gseg = (long long)blockIdx.x * kSegs + seg;
+        const long long off = gseg * a.levels * level_words;
+        if (off + (long long)a.levels * level_words > a.gstack_words) return;  // slab too small: never taken
+        stack = a.gstack + off;
+    }
     SetConst &K = Ks[seg];
     int loaded = -1;
     SegStats st;    // meaningful on lane 0
@@ -681,7 +688,7 @@ template <int LANES, int G, int SAVE>
 cudaError_t launch(const KoWork &a, cudaStream_t st)
 {
     const int level_words = state_words(G) * SAVE + 4;
-    const size_t smem = sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
+    const size_t smem = a.gstack ? 0 : sizeof(int) * (size_t)(kThreads / LANES) * a.levels * level_words;
     cudaError_t e = cudaFuncSetAttribute(fast_kernel<LANES, G, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -691,6 +698,10 @@ cudaError_t launch(const KoWork &a, cudaStream_t st)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast_kernel<LANES, G, SAVE>, kThreads, smem);
     if (e != cudaSuccess) return e;
     long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (a.gstack) {  // as many blocks as the slab holds segments for
+        const long long fit = a.gstack_words / ((long long)(kThreads / LANES) * a.levels * level_words);
+        if (blocks > fit) blocks = fit;
+    }
     const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
     const long long blocks_needed = (work + kThreads / LANES - 1) / (kThreads / LANES);
     if (blocks > blocks_needed) blocks = blocks_needed;
@@ -745,6 +756,24 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
         }
         fs->fb_bytes = kFallbackScratch;
     }
+    if (fs->stack_global) {
+        // pass 1: at most 8 blocks of 8 segments per SM, 16 saved lanes per level
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int lv = w.levels < 1 ? 1 : (w.levels > kMaxLevels ? kMaxLevels : w.levels);
+        const size_t need = sizeof(int) * (size_t)sms * 8 * 8 * lv * (state_words(kG) * 16 + 4);
+        if (fs->gstack_bytes < need) {
+            cudaFree(fs->gstack);
+            fs->gstack = nullptr;
+            fs->gstack_bytes = 0;
+            if (cudaMalloc(&fs->gstack, need) != cudaSuccess) {
+                cudaGetLastError();
+                return KO_ERR_NOMEM;
+            }
+            fs->gstack_bytes = need;
+        }
+    }
     FastBuf *fb = (FastBuf *)fs->buf;
     if (cudaMemsetAsync(fb, 0, sizeof(FastBuf), st) != cudaSuccess) return KO_ERR_CUDA;
     w.run_limit = fs->run_limit;
@@ -757,6 +786,8 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w.ov_list = fb->ov_list;
     w.item_list = nullptr;
     w.item_count = nullptr;
+    w.gstack = fs->stack_global ? (int *)fs->gstack : nullptr;
+    w.gstack_words = fs->stack_global ? (long long)(fs->gstack_bytes / sizeof(int)) : 0;
     cudaError_t e = fs->lanes == 16 ? launch<16, kG, 16>(w, st) : launch<32, kG, 16>(w, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -764,6 +795,8 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     }
     // pass 2: the items pass 1 abandoned, 32 lanes and 16 group slots per run
     KoWork w2 = w;
+    w2.gstack = nullptr;  // the wide pass keeps its (32-lane) node states in shared memory
+    w2.gstack_words = 0;
     w2.counter = &fb->counter[1];
     w2.item_list = fb->ov_list;
     w2.item_count = &fb->ov_count[0];
@@ -798,6 +831,9 @@ void ko_fast_release(KoFastState *fs)
     fs->ev0 = fs->ev1 = nullptr;
     cudaFree(fs->buf);
     cudaFree(fs->fb_scratch);
+    cudaFree(fs->gstack);
+    fs->gstack = nullptr;
+    fs->gstack_bytes = 0;
     fs->buf = nullptr;
     fs->fb_scratch = nullptr;
     fs->cap = 0;

@@ -37,6 +37,8 @@ struct KoWork {
     const unsigned long long *item_count;
     int levels;                       // saved DFS levels per segment
     int run_limit;                    // runs one simulation may hold
+    int *gstack;                      // non-null: DFS node states in this global slab, not shared memory
+    long long gstack_words;           // words of gstack (bounds the segments that may use it)
 };
 
 // Device-side state of the run-length simulator, owned by a handle or batch.
@@ -50,6 +52,9 @@ struct KoFastState {
     int levels = 4;             // saved DFS levels (items fix N - 1 - levels kernels)
     bool disabled = false;      // use the simple simulator only
     int run_limit = 32;         // cap on runs per simulation (tests force the hand-over)
+    int stack_global = 1;       // DFS node states in global memory (1) or shared memory (0)
+    void *gstack = nullptr;     // global slab for node states
+    size_t gstack_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last run-length launch
     double last_ms = -1.0;
     long long h2d = 0, d2h = 0;

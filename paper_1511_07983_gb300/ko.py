@@ -216,7 +216,7 @@ def ko_eval_all(g, out, stream=None):
     return _check(lib().ko_eval_all(g, _ptr(out), _stream(stream)), "ko_eval_all")
 
 
-KO_OPT_LANES, KO_OPT_LEVELS, KO_OPT_SIMPLE_ONLY, KO_OPT_RUN_LIMIT = 1, 2, 3, 4
+KO_OPT_LANES, KO_OPT_LEVELS, KO_OPT_SIMPLE_ONLY, KO_OPT_RUN_LIMIT, KO_OPT_STACK_GLOBAL = 1, 2, 3, 4, 5
 
 
 def ko_set_option(g, key, value):
@@ -461,7 +461,7 @@ class Gpu:
     def set_option(self, key, value):
         return ko_set_option(self.h, key, value)
 
-    def configure(self, lanes=None, levels=None, simple_only=None, run_limit=None):
+    def configure(self, lanes=None, levels=None, simple_only=None, run_limit=None, stack_global=None):
         if lanes is not None:
             self.set_option(KO_OPT_LANES, lanes)
         if levels is not None:
@@ -470,6 +470,8 @@ class Gpu:
             self.set_option(KO_OPT_SIMPLE_ONLY, int(bool(simple_only)))
         if run_limit is not None:
             self.set_option(KO_OPT_RUN_LIMIT, run_limit)
+        if stack_global is not None:
+            self.set_option(KO_OPT_STACK_GLOBAL, int(bool(stack_global)))
         return self
 
     def last_fallback_items(self):

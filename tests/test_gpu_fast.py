@@ -126,3 +126,18 @@ def test_autotune_choice_cache_and_exactness(ko, tmp_path):
     assert data["S16_N8"]["lanes"] == choice["lanes"] and data["S16_N8"]["levels"] == choice["levels"]
     with ko.Gpu.from_set(s) as g:   # second handle: served from the cache
         assert g.autotune(cache) == choice
+
+
+@pytest.mark.parametrize("lanes", [16, 32])
+@pytest.mark.parametrize("levels", [1, 3, 5])
+def test_global_node_stack_is_exact(ko, lanes, levels):
+    s = synth.gen_set("single8")
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=40320)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=lanes, levels=levels, stack_global=True)
+        assert np.array_equal(_all(g, 8), want)
+        r, hist = g.rank_order(None, nbins=4096)
+    h = oracle.heuristic(s.gpu, s.kernels)
+    st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h), makespans=want)
+    assert (r["min"], r["max"], r["n_equal"]) == (st["min"], st["max"], st["n_equal"])
+    assert np.array_equal(hist, st["hist"])
