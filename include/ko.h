@@ -176,9 +176,9 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 int64_t ko_get_option(const ko_gpu *g, int32_t key);
 
 /* Autotuner: times the run-length simulator on a calibration slice of this
- * set's exhaustive space (about 4M orders, at least 20k work items) for every
- * candidate (16 or 32 lanes per simulation; 1..min(N-1, 5) saved DFS levels,
- * skipping depths whose slice would exceed 40M orders), keeps the fastest
+ * set's exhaustive space (at least 16 work items per resident simulation and
+ * about 4M orders, at most 64M) for every candidate (16 or 32 lanes per
+ * simulation; 1..min(N-1, 5) saved DFS levels), keeps the fastest
  * and sets KO_OPT_LANES / KO_OPT_LEVELS on the
  * handle.  With cache_path (nullable) the choice is looked up first and
  * stored after, keyed by (N_SM class, N), in a small JSON file.  Synchronises

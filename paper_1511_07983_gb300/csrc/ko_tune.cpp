@@ -95,19 +95,20 @@ void write_cache(const char *path, const std::map<std::string, Choice> &m)
 
 }  // namespace
 
-// Calibration slice of a candidate depth: about 4M orders, but at least 20k
-// work items (enough to fill the GPU) unless the space is smaller; 0 when
-// such a slice would exceed 40M orders (too deep to be worth timing).
-long long ko_tune_items(int n, int levels)
+// Calibration slice of a candidate depth: at least 16 work items per
+// resident segment (so the tail of the slice does not bias deep candidates)
+// and about 4M orders, capped at 64M orders and at the whole space.
+long long ko_tune_items(int n, int levels, long long segments)
 {
     int d0 = n - 1 - levels;
     if (d0 < 0) d0 = 0;
     const long long items_all = kFact[n] / kFact[n - d0];
     const long long span = kFact[n - d0];
     long long items = (4000000 + span - 1) / span;
-    if (items < 20000) items = 20000;
+    if (items < 16 * segments) items = 16 * segments;
+    if (items * span > 64000000) items = 64000000 / span;
+    if (items < 1) items = 1;
     if (items > items_all) items = items_all;
-    if (items * span > 40000000 && items < items_all) return 0;
     return items;
 }
 
@@ -120,7 +121,11 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
     int d0 = n - 1 - levels;
     if (d0 < 0) d0 = 0;
     const long long span = kFact[n - d0];
-    const long long items = ko_tune_items(n, levels);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long segments = (long long)sms * 8 * (128 / lanes);  // 8 resident blocks of 128 threads
+    const long long items = ko_tune_items(n, levels, segments);
     if (items <= 0) return 0.0;
     KoChunk c{};
     c.count = items;
@@ -177,7 +182,6 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChu
     bool warmed = false;
     for (int lanes : {32, 16}) {
         for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
-            if (ko_tune_items(h.n, levels) <= 0) continue;
             const double r = ko_tune_measure(fs, h, d_set, d_chunk, d_acc, lanes, levels, warmed ? 1 : 2, st);
             warmed = true;
             if (r > best.rate) {
