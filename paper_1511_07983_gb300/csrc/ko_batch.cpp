@@ -215,7 +215,7 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
     none.chunks = b->d_chunks;
     none.nchunks = 1;
     none.n_items = 0;
-    none.levels = 1;
+    none.levels = b->levels_max;  // the deepest launch of the batch sizes the node-state slab
     if (ko_fast_launch(&b->fast, none, b->slab, b->cap_stream) != KO_OK ||
         cudaStreamSynchronize(b->cap_stream) != cudaSuccess) {
         cudaGetLastError();

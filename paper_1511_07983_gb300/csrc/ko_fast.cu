@@ -764,6 +764,13 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
         const int lv = w.levels < 1 ? 1 : (w.levels > kMaxLevels ? kMaxLevels : w.levels);
         const size_t need = sizeof(int) * (size_t)sms * 8 * 8 * lv * (state_words(kG) * 16 + 4);
         if (fs->gstack_bytes < need) {
+            // a stream being captured cannot take a free or a malloc: the
+            // caller must size the slab with an uncaptured launch first
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+                cudaGetLastError();
+                return KO_ERR_STATE;
+            }
             cudaFree(fs->gstack);
             fs->gstack = nullptr;
             fs->gstack_bytes = 0;
