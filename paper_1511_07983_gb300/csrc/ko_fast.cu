@@ -593,7 +593,7 @@ fast_kernel(KoWork a)
             }
         } else {
             d0 = ch.d0;
-            const unsigned long long base = (unsigned long long)local * c_fact[n - d0];
+            const unsigned long long base = (unsigned long long)(ch.list_off + local) * c_fact[n - d0];
             outpos = ch.out_off + (long long)base;
             lehmer_prefix(n, base, d0, perm, used);
         }

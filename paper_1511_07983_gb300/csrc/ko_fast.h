@@ -12,7 +12,9 @@ struct KoChunk {
     int d0;              // mode 0: kernels fixed by an item's prefix
     int mode;            // 0 = exhaustive prefixes, 1 = Lehmer index list, 2 = explicit rows
     int pad;
-    long long list_off;  // mode 1: entry of idx for the first item; mode 2: byte offset of its row
+    long long list_off;  // mode 0: item offset of the first item in the set's space (its first
+                         // order is Lehmer index list_off * (N - d0)!); mode 1: entry of idx for
+                         // the first item; mode 2: byte offset of its row
     long long out_off;   // added to the output position (mode 0: Lehmer index; 1/2: item)
 };
 

@@ -69,9 +69,9 @@ void ko_batch_free(ko_batch *b);
 // Autotuner internals (ko_tune.cpp).
 struct KoFastState;
 struct KoChunk;
-ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
-                      KoAccum *d_acc, const char *cache_path, cudaStream_t st, int *lanes_out,
-                      int *levels_out, double *rate_out);
+ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAccum *d_acc,
+                      const char *cache_path, cudaStream_t st, int *lanes_out, int *levels_out,
+                      double *rate_out);
 
 // Surrogate model internals (ko_model.cpp).
 ko_model *ko_model_new(uint64_t seed, ko_status *err);

@@ -314,7 +314,7 @@ fallback_kernel(KoWork w, void *scratch, size_t per_thread)
             bool ok = true;
             long long outpos;
             if (ch.mode == 0) {
-                const unsigned long long k = (unsigned long long)local * span + o;
+                const unsigned long long k = (unsigned long long)(ch.list_off + local) * span + o;
                 outpos = ch.out_off + (long long)k;
                 unrank(n, k, perm);
             } else if (ch.mode == 1) {

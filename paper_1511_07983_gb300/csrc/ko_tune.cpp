@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "ko_fast.h"
 #include "ko_internal.h"
@@ -95,47 +96,64 @@ void write_cache(const char *path, const std::map<std::string, Choice> &m)
 
 }  // namespace
 
-// Calibration slice of a candidate depth: at least 16 work items per
-// resident segment (so the tail of the slice does not bias deep candidates)
-// and about 4M orders, capped at 64M orders and at the whole space.
-long long ko_tune_items(int n, int levels, long long segments)
+// Calibration slice, the same orders for every candidate so that no depth is
+// timed on an easier part of the space: the whole space when N! <= 64M orders,
+// else kSliceChunks ranges of equal length spread evenly over the space, each
+// starting and ending on a multiple of 720 = 6! orders -- a multiple of the
+// span (levels + 1)! of every candidate depth (levels <= 5).
+constexpr int kSliceChunks = 16;
+constexpr long long kSliceOrders = 64000000;
+constexpr long long kSpanAll = 720;
+
+// Chunks of the slice for a candidate with prefix depth d0; returns the items.
+long long ko_tune_chunks(int n, int d0, std::vector<KoChunk> &out)
 {
-    int d0 = n - 1 - levels;
-    if (d0 < 0) d0 = 0;
-    const long long items_all = kFact[n] / kFact[n - d0];
+    out.clear();
     const long long span = kFact[n - d0];
-    long long items = (4000000 + span - 1) / span;
-    if (items < 16 * segments) items = 16 * segments;
-    if (items * span > 64000000) items = 64000000 / span;
-    if (items < 1) items = 1;
-    if (items > items_all) items = items_all;
-    return items;
+    const long long total = kFact[n];
+    if (total <= kSliceOrders) {
+        KoChunk c{};
+        c.count = total / span;
+        c.d0 = d0;
+        out.push_back(c);
+        return c.count;
+    }
+    const long long len = kSliceOrders / kSliceChunks / kSpanAll * kSpanAll;
+    long long first = 0;
+    for (int k = 0; k < kSliceChunks; k++) {
+        const long long start = (long long)((__int128)total * k / kSliceChunks / kSpanAll) * kSpanAll;
+        KoChunk c{};
+        c.first = first;
+        c.count = len / span;
+        c.d0 = d0;
+        c.list_off = start / span;
+        out.push_back(c);
+        first += c.count;
+    }
+    return first;
 }
 
-// Times one candidate on its calibration slice; returns orders per second
-// (0 on failure).  d_set / d_chunk / d_acc are device scratch of the caller.
-double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
+// Times one candidate on the calibration slice; returns orders per second
+// (0 on failure).  d_set / d_chunks / d_acc are device scratch of the caller
+// (d_chunks holds kSliceChunks entries).
+double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunks,
                        KoAccum *d_acc, int lanes, int levels, int reps, cudaStream_t st)
 {
     const int n = h.n;
     int d0 = n - 1 - levels;
     if (d0 < 0) d0 = 0;
     const long long span = kFact[n - d0];
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long segments = (long long)sms * 8 * (128 / lanes);  // 8 resident blocks of 128 threads
-    const long long items = ko_tune_items(n, levels, segments);
+    if (span > kSpanAll) return 0.0;
+    std::vector<KoChunk> chunks;
+    const long long items = ko_tune_chunks(n, d0, chunks);
     if (items <= 0) return 0.0;
-    KoChunk c{};
-    c.count = items;
-    c.d0 = d0;
-    c.mode = 0;
-    if (cudaMemcpyAsync(d_chunk, &c, sizeof(c), cudaMemcpyHostToDevice, st) != cudaSuccess) return 0.0;
+    if (cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(KoChunk) * chunks.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return 0.0;
     KoWork w{};
     w.sets = d_set;
-    w.chunks = d_chunk;
-    w.nchunks = 1;
+    w.chunks = d_chunks;
+    w.nchunks = (int)chunks.size();
     w.n_items = items;
     w.accs = d_acc;
     w.levels = n - 1 - d0 > 0 ? n - 1 - d0 : 1;
@@ -163,9 +181,9 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
 }
 
 // Pick lanes/levels for the handle's set; returns KO_OK and the choice.
-ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunk,
-                      KoAccum *d_acc, const char *cache_path, cudaStream_t st, int *lanes_out,
-                      int *levels_out, double *rate_out)
+ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAccum *d_acc,
+                      const char *cache_path, cudaStream_t st, int *lanes_out, int *levels_out,
+                      double *rate_out)
 {
     const std::string key = key_of(h);
     std::map<std::string, Choice> cache = read_cache(cache_path);
@@ -179,10 +197,15 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChu
     Choice best;
     best.rate = -1.0;
     const int max_levels = h.n - 1 < 5 ? h.n - 1 : 5;
+    KoChunk *d_chunks = nullptr;
+    if (cudaMalloc((void **)&d_chunks, sizeof(KoChunk) * kSliceChunks) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
     bool warmed = false;
     for (int lanes : {32, 16}) {
         for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
-            const double r = ko_tune_measure(fs, h, d_set, d_chunk, d_acc, lanes, levels, warmed ? 1 : 2, st);
+            const double r = ko_tune_measure(fs, h, d_set, d_chunks, d_acc, lanes, levels, warmed ? 1 : 2, st);
             warmed = true;
             if (r > best.rate) {
                 best.rate = r;
@@ -191,6 +214,7 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChu
             }
         }
     }
+    cudaFree(d_chunks);
     if (best.rate <= 0.0) return KO_ERR_CUDA;
     cache[key] = best;
     write_cache(cache_path, cache);
