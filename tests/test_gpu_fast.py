@@ -141,3 +141,30 @@ def test_global_node_stack_is_exact(ko, lanes, levels):
     st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h), makespans=want)
     assert (r["min"], r["max"], r["n_equal"]) == (st["min"], st["max"], st["n_equal"])
     assert np.array_equal(hist, st["hist"])
+
+
+@pytest.mark.parametrize("case", ["sm1024", "one_block_per_sm", "no_smem", "huge_durations", "bk32_tiny_sm"])
+def test_edge_gpus_match_oracle(ko, case):
+    if case == "sm1024":        # many runs: hand-over to the wide pass and the simple simulator
+        s = synth.random_set(41, 5, gpu=(1024, 65536, 233472, 64, 32), blk=(100, 3000), c=(1000, 50000))
+    elif case == "one_block_per_sm":
+        s = synth.random_set(42, 6, gpu=(7, 65536, 233472, 64, 1), blk=(1, 30))
+    elif case == "no_smem":
+        s = synth.random_set(43, 6, gpu=(13, 65536, 49152, 64, 16), blk=(5, 80))
+        s.kernels[:, 1] = 0
+    elif case == "huge_durations":  # durations reach 2^31: the run-length path does not apply
+        s = synth.random_set(44, 5, gpu=(13, 65536, 49152, 64, 16), blk=(5, 60), c=(1 << 19, 1 << 20),
+                             c_cap=1, m_cap=1)
+    else:
+        s = synth.random_set(45, 6, gpu=(2, 65536, 233472, 64, 32), blk=(1, 40))
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=math.factorial(s.n))
+    with ko.Gpu.from_set(s) as g:
+        got = _all(g, s.n)
+        assert np.array_equal(got, want), case
+        h = oracle.heuristic(s.gpu, s.kernels)
+        r, hist = g.rank_order(h, nbins=128)
+    st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h), nbins=128,
+                                 makespans=want)
+    assert (r["min"], r["max"], r["n_better"], r["n_equal"], r["n_worse"]) == \
+        (st["min"], st["max"], st["n_better"], st["n_equal"], st["n_worse"])
+    assert np.array_equal(hist, st["hist"])
