@@ -73,6 +73,13 @@ def lib():
                                               P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_int64)]
             L.or_heuristic.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32)]
             L.or_heuristic.restype = ctypes.c_int
+            L.or_heuristic_fp.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), ctypes.c_int,
+                                          P(ctypes.c_int32)]
+            L.or_heuristic_fp.restype = ctypes.c_int
+            L.or_local_search.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32),
+                                          ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int64),
+                                          P(ctypes.c_int64)]
+            L.or_local_search.restype = ctypes.c_int
             L.or_score_matrix.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_double)]
             L.or_bounds.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64),
                                     P(ctypes.c_int64), P(ctypes.c_int64)]
@@ -152,6 +159,33 @@ def heuristic(gpu, kernels) -> list[int]:
     out = np.zeros(max(k.shape[0], 1), dtype=np.int32)
     lib().or_heuristic(ctypes.byref(g), k.shape[0], _p(k, ctypes.c_int64), _p(out, ctypes.c_int32))
     return [int(v) for v in out[:k.shape[0]]]
+
+
+def heuristic_fp(gpu, kernels, per_block: bool) -> list[int]:
+    """Algorithm 1 with the per-SM (False) or per-block (True) footprint reading."""
+    k = _kern(kernels)
+    g = _gpu(gpu)
+    out = np.zeros(max(k.shape[0], 1), dtype=np.int32)
+    lib().or_heuristic_fp(ctypes.byref(g), k.shape[0], _p(k, ctypes.c_int64), int(bool(per_block)),
+                          _p(out, ctypes.c_int32))
+    return [int(v) for v in out[:k.shape[0]]]
+
+
+def local_search(gpu, kernels, start, moves: bool = True, max_iters: int = 1 << 20):
+    """Steepest-descent hill climbing from `start` (swaps, plus moves if
+    `moves`), every candidate scored exactly.  Returns (order, makespan,
+    steps, orders scored)."""
+    k = _kern(kernels)
+    g = _gpu(gpu)
+    n = k.shape[0]
+    st = np.ascontiguousarray(np.asarray(start, dtype=np.int32).reshape(n))
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    ms = ctypes.c_int64(0)
+    ev = ctypes.c_int64(0)
+    steps = lib().or_local_search(ctypes.byref(g), n, _p(k, ctypes.c_int64), _p(st, ctypes.c_int32),
+                                  int(bool(moves)), int(max_iters), _p(out, ctypes.c_int32),
+                                  ctypes.byref(ms), ctypes.byref(ev))
+    return [int(v) for v in out[:n]], int(ms.value), int(steps), int(ev.value)
 
 
 def heuristic_rounds(gpu, kernels) -> int:

@@ -13,7 +13,10 @@
  *   or_makespan              block-by-block dispatch simulation of one order
  *                            (Sec. 2 dispatch rule; duration rule = reading A1).
  *   or_makespans_idx         many orders by Lehmer index, pthreads over ranges.
- *   or_heuristic             Algorithm 1 (ScoreGen, ProfileCombine, rounds).
+ *   or_heuristic             Algorithm 1 (ScoreGen, ProfileCombine, rounds);
+ *   or_heuristic_fp          the same with a choice of footprint reading.
+ *   or_local_search          steepest-descent hill climbing from an order,
+ *                            every candidate scored by or_makespan.
  *   or_bounds                work/capacity lower bound and serial upper bound.
  *
  * Model (Sec. 2 and the readings recorded in the design notes):
@@ -263,10 +266,12 @@ typedef struct {
     int64_t inst, mem;      /* sum N_tblk*c, sum N_tblk*m */
 } profile;
 
-static profile profile_of(const or_gpu *g, const or_kernel *kk)
+/* per_block = 1 is the alternative reading of the resource terms: one block's
+ * registers, shared memory and warps (footprint multiplier q = 1). */
+static profile profile_of_fp(const or_gpu *g, const or_kernel *kk, int per_block)
 {
     profile pr;
-    int64_t q = (kk->n_tblk + g->n_sm - 1) / g->n_sm;
+    int64_t q = per_block ? 1 : (kk->n_tblk + g->n_sm - 1) / g->n_sm;
     pr.fr = q * kk->n_reg;
     pr.fs = q * kk->n_shm;
     pr.fw = q * kk->n_warp;
@@ -275,6 +280,8 @@ static profile profile_of(const or_gpu *g, const or_kernel *kk)
     pr.mem = kk->n_tblk * kk->m;
     return pr;
 }
+
+static profile profile_of(const or_gpu *g, const or_kernel *kk) { return profile_of_fp(g, kk, 0); }
 
 /* ProfileCombine(K_a, K_b): summed footprints, summed instruction and memory
  * totals (the weighted-harmonic R_comb follows from them). */
@@ -317,13 +324,14 @@ static double score_pair(const or_gpu *g, profile a, profile b)
 }
 
 /* Writes the launch order (n kernel indices) to order_out.  Returns the number
- * of execution rounds. */
-int or_heuristic(const or_gpu *g, int n, const or_kernel *k, int32_t *order_out)
+ * of execution rounds.  per_block selects the footprint reading (see
+ * profile_of_fp); or_heuristic is the per-SM reading. */
+int or_heuristic_fp(const or_gpu *g, int n, const or_kernel *k, int per_block, int32_t *order_out)
 {
     profile pr[64];
     int remaining[64];
     double score[64][64];
-    for (int i = 0; i < n; i++) { pr[i] = profile_of(g, &k[i]); remaining[i] = 1; }
+    for (int i = 0; i < n; i++) { pr[i] = profile_of_fp(g, &k[i], per_block); remaining[i] = 1; }
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++)
             score[i][j] = (i == j) ? 0.0 : score_pair(g, pr[i], pr[j]);
@@ -379,6 +387,75 @@ int or_heuristic(const or_gpu *g, int n, const or_kernel *k, int32_t *order_out)
         for (int q = 0; q < rn; q++) order_out[out++] = round_members[q];
     }
     return rounds;
+}
+
+int or_heuristic(const or_gpu *g, int n, const or_kernel *k, int32_t *order_out)
+{
+    return or_heuristic_fp(g, n, k, 0, order_out);
+}
+
+/* ------------------------------------------------- exact local search --- */
+/*
+ * Steepest-descent hill climbing over launch orders, every candidate scored
+ * exactly by or_makespan (the "reorder, then measure" loop of Sec. 6 run as a
+ * search instead of an enumeration).  The neighbours of an order p are, in
+ * this order:
+ *   swaps  q = 0 .. n(n-1)/2-1:  exchange positions (i, j), i < j, pairs in
+ *          lexicographic order;
+ *   moves  (hood = 1 only) q = n(n-1)/2 + from*(n-1) + t:  take the kernel at
+ *          position `from` out and reinsert it at position `to`, where `to`
+ *          runs over 0..n-1 without `from` (to = t if t < from, else t + 1).
+ * One step evaluates every neighbour and moves to the lowest makespan, the
+ * lowest q among equals, only if it is strictly below the current makespan.
+ * Stops at a local optimum or after max_iters steps.  Returns the number of
+ * steps taken; *evals_out counts the orders scored (start included).
+ */
+static void neighbour(int n, const int32_t *p, int q, int32_t *out)
+{
+    int swaps = n * (n - 1) / 2;
+    for (int i = 0; i < n; i++) out[i] = p[i];
+    if (q < swaps) {
+        int i = 0, rem = q;
+        while (rem >= n - 1 - i) { rem -= n - 1 - i; i++; }
+        int j = i + 1 + rem;
+        int32_t t = out[i]; out[i] = out[j]; out[j] = t;
+        return;
+    }
+    int mv = q - swaps, from = mv / (n - 1), t = mv % (n - 1);
+    int to = t < from ? t : t + 1;
+    /* remove, then insert */
+    int32_t tmp[64];
+    int w = 0;
+    for (int i = 0; i < n; i++) if (i != from) tmp[w++] = p[i];
+    w = 0;
+    for (int i = 0; i < n; i++) out[i] = (i == to) ? p[from] : tmp[w++];
+}
+
+int or_local_search(const or_gpu *g, int n, const or_kernel *k, const int32_t *start, int hood,
+                    int max_iters, int32_t *order_out, int64_t *makespan_out, int64_t *evals_out)
+{
+    int32_t cur[64], cand[64], best_nb[64];
+    int nq = n * (n - 1) / 2 + (hood ? n * (n - 1) : 0);
+    for (int i = 0; i < n; i++) cur[i] = start[i];
+    int64_t cur_ms = or_makespan(g, n, k, cur), evals = 1;
+    int steps = 0;
+    while (steps < max_iters && nq > 0) {
+        int64_t best = -1;
+        for (int q = 0; q < nq; q++) {
+            neighbour(n, cur, q, cand);
+            int64_t ms = or_makespan(g, n, k, cand);
+            evals++;
+            if (best < 0 || ms < best) { best = ms; memcpy(best_nb, cand, sizeof(int32_t) * n); }
+        }
+        if (best >= cur_ms) break;
+        cur_ms = best;
+        memcpy(cur, best_nb, sizeof(int32_t) * n);
+        steps++;
+    }
+    for (int i = 0; i < n; i++) order_out[i] = cur[i];
+    *makespan_out = cur_ms;
+    *evals_out = evals;
+    return steps;
 }
 
 /* Score matrix as Algorithm 1 builds it (for tests); row-major [n, n]. */

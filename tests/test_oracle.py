@@ -170,7 +170,7 @@ def test_empty_set():
 
 # ------------------------------------------------------------ Algorithm 1 ---
 
-@pytest.mark.parametrize("name", ["W1", "W2", "W3", "W4"])
+@pytest.mark.parametrize("name", ["W1", "W2", "W3", "W4", "W5"])
 def test_heuristic_hand_traced(name):
     c = CASES[name]
     assert oracle.heuristic(c["gpu"], c["kernels"]) == c["heuristic"]
