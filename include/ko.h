@@ -124,6 +124,16 @@ ko_status ko_bounds(ko_gpu *g, int64_t *lb, int64_t *ub);
  * R_i = c_i / m_i, R_B = Ccap / Mcap, R_comb = sum(N_tblk c) / sum(N_tblk m). */
 ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out);
 
+/* Algorithm 1 under a chosen reading of its resource terms (Sec. 5, the
+ * ScoreGen resource fractions and the "fits within an execution round" test):
+ *   KO_HEUR_PER_SM     per-SM footprints ceil(N_tblk / N_SM) x (regs, smem,
+ *                      warps, 1) -- what ko_heuristic_order uses;
+ *   KO_HEUR_PER_BLOCK  one block's (regs, smem, warps, 1).
+ * Writes N kernel ids to order_out (host).  KO_ERR_ARG for another value. */
+#define KO_HEUR_PER_SM 0
+#define KO_HEUR_PER_BLOCK 1
+ko_status ko_heuristic_order_ex(ko_gpu *g, int32_t reading, int32_t *order_out);
+
 /* Makespans of n launch orders, written to makespan_out[n] (host or device).
  * Exactly one of idx / orders is non-NULL:
  *   idx     n Lehmer indices in [0, N!)   (N <= 20), host or device;
@@ -308,6 +318,24 @@ ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t to
  * orders simulated exactly; the best one is returned. */
 ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
                            int64_t *best_makespan, double *gpu_ms, void *stream);
+
+/* Exact local search: steepest-descent hill climbing over launch orders, the
+ * heuristic-then-improve step that Sec. 6's exhaustive measurement suggests
+ * (the paper itself stops at Algorithm 1).  Starts from `start` (host, N ids;
+ * NULL = the Algorithm 1 order).  Each step simulates every neighbour of the
+ * current order exactly -- the N(N-1)/2 swaps of two positions, pairs (i, j),
+ * i < j, in lexicographic order, then, if moves != 0, the N(N-1) moves of the
+ * kernel at position `from` to position `to` (from-major, `to` ascending) --
+ * and moves to the lowest makespan (lowest neighbour index among equals) only
+ * if it is strictly lower.  Stops at a local optimum or after max_iters steps
+ * (0..2^20).  Outputs (host): order_out[N], *makespan_out; steps_out,
+ * evals_out (orders simulated, start included) and gpu_ms (elapsed time on
+ * `stream`) are nullable.  Synchronises `stream`.  KO_ERR_ARG if start is not
+ * a permutation; KO_ERR_OVERFLOW if the set exceeds the run-length
+ * simulator's limits. */
+ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_t max_iters, int32_t *order_out,
+                          int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out, double *gpu_ms,
+                          void *stream);
 
 /* Model options.  KO_MODEL_OPT_TC: tensor-core path of the inference
  * forward (ko_model_predict, ko_surrogate_propose, ko_surrogate_search) --

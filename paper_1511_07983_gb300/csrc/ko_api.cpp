@@ -289,6 +289,14 @@ ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out)
     return ok();
 }
 
+ko_status ko_heuristic_order_ex(ko_gpu *g, int32_t reading, int32_t *order_out)
+{
+    if (!g || (!order_out && g->h.n > 0) || (reading != KO_HEUR_PER_SM && reading != KO_HEUR_PER_BLOCK))
+        return fail(KO_ERR_ARG);
+    if (g->h.n > 0) ko_heuristic_host(g->h, order_out, reading == KO_HEUR_PER_BLOCK);
+    return ok();
+}
+
 ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
                          int64_t *makespan_out, void *stream)
 {
@@ -746,6 +754,20 @@ ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *
     g->frozen = true;
     ko_status s = ko_random_search_set(&g->fast, g->h, n_orders, seed, best_order, best_makespan, gpu_ms,
                                        (cudaStream_t)stream);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_t max_iters, int32_t *order_out,
+                          int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out, double *gpu_ms,
+                          void *stream)
+{
+    if (!g || !order_out || !makespan_out || g->h.n < 1) return fail(KO_ERR_ARG);
+    g->frozen = true;
+    std::vector<int32_t> st0(g->h.n);
+    if (start) std::copy(start, start + g->h.n, st0.begin());
+    else ko_heuristic_host(g->h, st0.data());
+    ko_status s = ko_local_search_set(&g->fast, g->h, st0.data(), moves != 0, max_iters, order_out, makespan_out,
+                                      steps_out, evals_out, gpu_ms, (cudaStream_t)stream);
     return s ? fail(s) : ok();
 }
 

@@ -3,7 +3,8 @@
 //
 // Algorithm 1 readings (the paper leaves these open):
 //   * resource terms use a kernel's per-SM footprint: q = ceil(N_tblk / N_SM)
-//     blocks, i.e. q * (registers, shared memory, warps, 1 block slot);
+//     blocks, i.e. q * (registers, shared memory, warps, 1 block slot); the
+//     per-block reading (q = 1) is selectable for comparison;
 //   * "fits within an execution round" = summed footprints within the four
 //     per-SM limits;
 //   * R_i = c_i / m_i; R_B = Ccap / Mcap; a combined profile carries the sums
@@ -31,9 +32,10 @@ struct Footprint {
     int64_t inst, mem;             // sum N_tblk * c, sum N_tblk * m
 };
 
-Footprint footprint(const KoSet &h, const KoKern &k)
+// per_block: the alternative reading, one block's resources (q = 1)
+Footprint footprint(const KoSet &h, const KoKern &k, bool per_block)
 {
-    const int64_t q = ((int64_t)k.b + h.S - 1) / h.S;
+    const int64_t q = per_block ? 1 : ((int64_t)k.b + h.S - 1) / h.S;
     return Footprint{q * k.r, q * k.s, q * k.w, q, (int64_t)k.b * k.c, (int64_t)k.b * k.m};
 }
 
@@ -75,11 +77,11 @@ double pair_score(const KoSet &h, const Footprint &x, const Footprint &y)
 
 }  // namespace
 
-int ko_heuristic_host(const KoSet &h, int32_t *order_out)
+int ko_heuristic_host(const KoSet &h, int32_t *order_out, bool per_block)
 {
     const int n = h.n;
     std::vector<Footprint> fp(n);
-    for (int i = 0; i < n; i++) fp[i] = footprint(h, h.k[i]);
+    for (int i = 0; i < n; i++) fp[i] = footprint(h, h.k[i], per_block);
     // ScoreMatrix over all pairs, computed once
     std::vector<double> score((size_t)n * n, 0.0);
     for (int i = 0; i < n; i++)

@@ -100,7 +100,10 @@ ko_status ko_noalloc_eval(const KoSet &h, const int8_t *d_orders, long long coun
 size_t ko_noalloc_scratch_bytes();
 
 // Host-side Algorithm 1; returns the number of execution rounds.
-int ko_heuristic_host(const KoSet &h, int32_t *order_out);
+int ko_heuristic_host(const KoSet &h, int32_t *order_out, bool per_block = false);
+ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *start, bool moves, int max_iters,
+                              int32_t *order_out, int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out,
+                              double *gpu_ms, cudaStream_t st);
 
 // Host-side bounds; returns false if the upper bound overflows 62 bits.
 bool ko_bounds_host(const KoSet &h, int64_t *lb, int64_t *ub);

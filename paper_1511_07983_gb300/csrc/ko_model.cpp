@@ -692,6 +692,90 @@ ko_status ko_random_search_set(KoFastState *fs, const KoSet &h, long long n_orde
     return s;
 }
 
+// Steepest-descent hill climbing with exact scoring.  Neighbours of the
+// current order come from the neighbours kernel (swaps of two positions, then
+// moves of one kernel to another position); every one is simulated exactly,
+// the lowest makespan wins (lowest neighbour index among equals) and the walk
+// moves only on a strict improvement.  One step = one H2D of the current order,
+// two launches and one D2H of the neighbours' makespans.
+ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *start, bool moves, int max_iters,
+                              int32_t *order_out, int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out,
+                              double *gpu_ms, cudaStream_t st)
+{
+    const int n = h.n;
+    if (n < 1 || max_iters < 0 || max_iters > (1 << 20)) return KO_ERR_ARG;
+    if (!ko_fast_applicable(h)) return KO_ERR_OVERFLOW;
+    std::vector<int8_t> cur(kMaxK, 0);
+    {
+        std::vector<char> seen(n, 0);
+        for (int i = 0; i < n; i++) {
+            if (start[i] < 0 || start[i] >= n || seen[start[i]]) return KO_ERR_ARG;
+            seen[start[i]] = 1;
+            cur[i] = (int8_t)start[i];
+        }
+    }
+    const KoSet *hs[1] = {&h};
+    SetTables tb;
+    ko_status s = build_tables(hs, 1, &tb, st);
+    if (s) return s;
+    const int swaps = n * (n - 1) / 2, per = swaps + n * (n - 1);
+    const int nq = moves ? per : swaps;
+    int8_t *base = nullptr, *nb = nullptr;
+    int64_t *ms = nullptr;
+    KoChunk *d_chunk = nullptr;
+    if (!dalloc(&base, kMaxK) || !dalloc(&nb, (size_t)(per > 0 ? per : 1) * kMaxK) ||
+        !dalloc(&ms, (size_t)(per > 0 ? per : 1) + 1) || !dalloc(&d_chunk, 1))
+        s = KO_ERR_NOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int64_t cur_ms = -1, evals = 0;
+    int steps = 0;
+    std::vector<int64_t> hm((size_t)(nq > 0 ? nq : 1));
+    if (!s) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        if (cudaMemcpyAsync(base, cur.data(), kMaxK, cudaMemcpyHostToDevice, st) != cudaSuccess) s = KO_ERR_CUDA;
+        if (!s) s = exact_rows(fs, tb.sets, h, 0, base, 1, ms + per, d_chunk, st);
+        if (!s && (cudaMemcpyAsync(&cur_ms, ms + per, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                   cudaStreamSynchronize(st) != cudaSuccess))
+            s = KO_ERR_CUDA;
+        if (!s && cur_ms < 0) s = KO_ERR_STATE;
+        evals = 1;
+        while (!s && steps < max_iters && nq > 0) {
+            if (cudaMemcpyAsync(base, cur.data(), kMaxK, cudaMemcpyHostToDevice, st) != cudaSuccess) { s = KO_ERR_CUDA; break; }
+            if ((s = cuda_ok(ko_mlp_neighbours(base, 1, n, nb, st)))) break;
+            if ((s = exact_rows(fs, tb.sets, h, 0, nb, nq, ms, d_chunk, st))) break;
+            if (cudaMemcpyAsync(hm.data(), ms, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) { s = KO_ERR_CUDA; break; }
+            evals += nq;
+            int bq = -1;
+            for (int q = 0; q < nq; q++) {
+                if (hm[q] < 0) { s = KO_ERR_STATE; break; }
+                if (bq < 0 || hm[q] < hm[bq]) bq = q;
+            }
+            if (s || hm[bq] >= cur_ms) break;
+            if (cudaMemcpy(cur.data(), nb + (size_t)bq * kMaxK, kMaxK, cudaMemcpyDeviceToHost) != cudaSuccess) { s = KO_ERR_CUDA; break; }
+            cur_ms = hm[bq];
+            steps++;
+        }
+        cudaEventRecord(e1, st);
+        if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;
+    }
+    if (!s) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (gpu_ms) *gpu_ms = t;
+        for (int i = 0; i < n; i++) order_out[i] = cur[i];
+        *makespan_out = cur_ms;
+        if (steps_out) *steps_out = steps;
+        if (evals_out) *evals_out = evals;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base); cudaFree(nb); cudaFree(ms); cudaFree(d_chunk);
+    return s;
+}
+
 // Features of explicit orders of one set (encoder output as floats), for tests.
 ko_status ko_model_features(const KoSet &h, const int8_t *orders, long long n, float *x_out, cudaStream_t st)
 {

@@ -93,6 +93,11 @@ _SIGNATURES = {
     "ko_random_search": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
+    "ko_heuristic_order_ex": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "ko_local_search": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "ko_model_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -186,6 +191,17 @@ def ko_heuristic_order(g):
     n = ko_num_kernels(g)
     out = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().ko_heuristic_order(g, _ptr(out)), "ko_heuristic_order")
+    return out[:n]
+
+
+KO_HEUR_PER_SM = 0
+KO_HEUR_PER_BLOCK = 1
+
+
+def ko_heuristic_order_ex(g, reading):
+    n = ko_num_kernels(g)
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().ko_heuristic_order_ex(g, reading, _ptr(out)), "ko_heuristic_order_ex")
     return out[:n]
 
 
@@ -418,6 +434,21 @@ def ko_random_search(g, n_orders, seed=0, stream=None):
     return order[:g.n], ms.value, t.value
 
 
+def ko_local_search(g, start=None, moves=True, max_iters=1 << 20, stream=None):
+    """Exact steepest-descent hill climbing; returns (order, makespan, steps,
+    orders simulated, elapsed ms)."""
+    n = g.n
+    st = None
+    if start is not None:
+        st = np.ascontiguousarray(np.asarray(start, dtype=np.int32).reshape(n))
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    ms, steps, evals, t = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+    _check(lib().ko_local_search(g.h, _ptr(st) if st is not None else None, int(bool(moves)), max_iters,
+                                 _ptr(order), ctypes.byref(ms), ctypes.byref(steps), ctypes.byref(evals),
+                                 ctypes.byref(t), _stream(stream)), "ko_local_search")
+    return order[:n], ms.value, steps.value, evals.value, t.value
+
+
 # ------------------------------------------------------------ convenience
 
 class Gpu:
@@ -446,8 +477,13 @@ class Gpu:
     def bounds(self):
         return ko_bounds(self.h)
 
-    def heuristic_order(self):
-        return ko_heuristic_order(self.h)
+    def heuristic_order(self, reading=KO_HEUR_PER_SM):
+        if reading == KO_HEUR_PER_SM:
+            return ko_heuristic_order(self.h)
+        return ko_heuristic_order_ex(self.h, reading)
+
+    def local_search(self, start=None, moves=True, max_iters=1 << 20, stream=None):
+        return ko_local_search(self, start=start, moves=moves, max_iters=max_iters, stream=stream)
 
     def eval_orders(self, idx=None, orders=None, out=None, stream=None):
         return ko_eval_orders(self.h, idx=idx, orders=orders, out=out, stream=stream)

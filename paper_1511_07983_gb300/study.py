@@ -1,0 +1,92 @@
+"""Launch-order strategies ranked against the whole permutation space.
+
+For each set, every one of the N! orders is simulated (ko_eval_all) and each
+strategy's order is placed in that ranking: its percentile
+100 * #{orders with makespan >= M} / N! (the Table 3 percentile of Sec. 6),
+its deviation (M - optimum) / optimum, and whether it is optimal.  The
+strategies are Algorithm 1 under the two readings of its resource terms
+(per-SM and per-block footprints, Sec. 5) and exact steepest-descent local
+search (swaps, or swaps and moves) started from Algorithm 1's order or from
+the order the kernels were added in.
+
+    python -m paper_1511_07983_gb300.study [--sets10 64] [--n11 16] [--json out.json]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import ko, synth
+
+STRATEGIES = ("alg1_per_sm", "alg1_per_block", "ls_swap_from_alg1", "ls_swap_move_from_alg1",
+              "ls_swap_move_from_identity")
+
+
+def rank_set(s) -> dict:
+    """Percentile, deviation and search cost of every strategy on one set."""
+    import torch
+    n = s.n
+    with ko.Gpu.from_set(s) as g:
+        every = torch.empty(math.factorial(n), dtype=torch.int64, device="cuda")
+        g.eval_all(every)
+        torch.cuda.synchronize()
+        best = int(every.min().item())
+        orders, cost = {}, {}
+        orders["alg1_per_sm"] = g.heuristic_order(ko.KO_HEUR_PER_SM)
+        orders["alg1_per_block"] = g.heuristic_order(ko.KO_HEUR_PER_BLOCK)
+        for name, start, moves in (("ls_swap_from_alg1", None, False), ("ls_swap_move_from_alg1", None, True),
+                                   ("ls_swap_move_from_identity", list(range(n)), True)):
+            o, _, steps, evals, ms = g.local_search(start=start, moves=moves)
+            orders[name] = o
+            cost[name] = {"steps": steps, "orders_simulated": evals, "gpu_ms": ms}
+        rows = np.stack([np.asarray(orders[k], dtype=np.int8) for k in STRATEGIES])
+        mk = g.eval_orders(orders=rows)
+        out = {"n": n, "n_sm": int(s.gpu[0]), "optimum": best, "worst": int(every.max().item())}
+        for k, m in zip(STRATEGIES, np.asarray(mk).tolist()):
+            pct = 100.0 * int((every >= m).sum().item()) / every.numel()
+            out[k] = {"makespan": int(m), "percentile": pct, "deviation": (m - best) / best,
+                      "optimal": bool(m == best), **cost.get(k, {})}
+        del every
+    return out
+
+
+def summarise(rows: list[dict]) -> dict:
+    out = {}
+    for k in STRATEGIES:
+        v = [r[k] for r in rows]
+        out[k] = {"mean_percentile": float(np.mean([x["percentile"] for x in v])),
+                  "mean_deviation": float(np.mean([x["deviation"] for x in v])),
+                  "optimal": int(sum(x["optimal"] for x in v)), "sets": len(v)}
+        if "orders_simulated" in v[0]:
+            out[k]["mean_orders_simulated"] = float(np.mean([x["orders_simulated"] for x in v]))
+            out[k]["mean_gpu_ms"] = float(np.mean([x["gpu_ms"] for x in v]))
+    return out
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sets10", type=int, default=64, help="N=10 sets on the 15-SM GPU")
+    ap.add_argument("--n11", type=int, default=16, help="N=11 sets on the 148-SM GPU")
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args(argv)
+    groups = {"sets10 (N=10, 15 SMs)": [synth.gen_set("sets10", i) for i in range(a.sets10)],
+              "N=11, 148 SMs": [synth.gen_set("single12", i, n=11) for i in range(a.n11)]}
+    report = {}
+    for name, sets in groups.items():
+        if not sets:
+            continue
+        t0 = time.time()
+        rows = [rank_set(s) for s in sets]
+        report[name] = {"summary": summarise(rows), "wall_s": time.time() - t0, "sets": rows}
+        print(json.dumps({name: report[name]["summary"]}, indent=1), flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(report, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -93,6 +93,22 @@ def test_heuristic_hand_traces(ko):
         assert g.heuristic_order().tolist() == c["heuristic"], c["name"]
 
 
+def test_heuristic_per_block_reading_matches_oracle(ko):
+    for s in _sets():
+        with ko.Gpu.from_set(s) as g:
+            assert g.heuristic_order(ko.KO_HEUR_PER_BLOCK).tolist() == oracle.heuristic_fp(s.gpu, s.kernels, True)
+            assert g.heuristic_order(ko.KO_HEUR_PER_SM).tolist() == oracle.heuristic(s.gpu, s.kernels)
+    import json
+    cases = json.load(open(os.path.join(ROOT, "tests", "golden", "hand_traces.json")))["cases"]
+    c = [c for c in cases if c["name"] == "W5"][0]
+    g = ko.Gpu(*c["gpu"][:5], c_cap=c["gpu"][5], m_cap=c["gpu"][6])
+    for row in c["kernels"]:
+        g.add_kernel(*row)
+    assert g.heuristic_order(ko.KO_HEUR_PER_BLOCK).tolist() == c["heuristic_per_block"]
+    with pytest.raises(ko.KoError):
+        ko.ko_heuristic_order_ex(g.h, 2)
+
+
 def test_bounds_match_oracle(ko):
     for s in _sets():
         with ko.Gpu.from_set(s) as g:
