@@ -19,9 +19,11 @@ Multi-GPU runs are independent replicas (one per rank); see the design doc.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -139,6 +141,25 @@ def placements_per_exhaustive(kernels) -> int:
     n = len(kernels)
     total_blocks = int(sum(int(k[3]) for k in kernels))
     return sum(math.factorial(n - 1) // math.factorial(n - d) for d in range(1, n + 1)) * total_blocks
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the run-length kernel from the committed ncu
+    summary, or None when no summary covers this workload or the kernel's
+    sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"fast_kernel_{workload}_dram.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mb = re.search(r"^- bytes per launch: (\d+)$", text, re.M)
+    mh = re.search(r"^- source sha256 \(ko_fast.cu \+ ko_fast.h\): ([0-9a-f]{64})$", text, re.M)
+    if not mb or not mh:
+        return None
+    h = hashlib.sha256()
+    for f in ("ko_fast.cu", "ko_fast.h"):
+        with open(os.path.join(ROOT, "paper_1511_07983_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return int(mb.group(1)) if h.hexdigest() == mh.group(1) else None
 
 
 def measured_peaks():
@@ -288,13 +309,7 @@ def run_ours(a):
     placements = placements_per_exhaustive(kset.kernels.tolist())
     kernel_s = statistics.mean(sim_ms) / 1e3
     achieved = placements * OPS_PER_PLACEMENT / kernel_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(a.workload)
-        except ValueError:
-            traffic = None
+    traffic = measured_traffic(a.workload)
     cb = cpu_baseline(kset, a.cpu_sample) if world == 1 else None
     sur = None
     if a.surrogate and world == 1:

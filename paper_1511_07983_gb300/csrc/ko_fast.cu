@@ -640,7 +640,8 @@ fast_kernel(KoWork a)
             if (depth + 1 == n) {
                 const long long ms = sim.finish(K);
                 if (sim.sg.lane == 0) {
-                    if (a.out) a.out[outpos + leaf] = ms;
+                    // evict-first: the makespan stream must not push the node-state slab out of L2
+                    if (a.out) __stcs((long long *)&a.out[outpos + leaf], (long long)ms);
                     const unsigned long long u = (unsigned long long)ms;
                     imin = u < imin ? u : imin;
                     imax = u > imax ? u : imax;

@@ -51,3 +51,22 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"])
     assert bench.main() == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_figure_only_for_unchanged_kernel_sources(tmp_path, monkeypatch):
+    import bench
+    prof = tmp_path / "profiles"
+    csrc = tmp_path / "paper_1511_07983_gb300" / "csrc"
+    prof.mkdir()
+    csrc.mkdir(parents=True)
+    (csrc / "ko_fast.cu").write_text("kernel A")
+    (csrc / "ko_fast.h").write_text("header")
+    import hashlib
+    good = hashlib.sha256(b"kernel A" + b"header").hexdigest()
+    (prof / "fast_kernel_w_dram.md").write_text(
+        "x\n- bytes per launch: 1234\n- source sha256 (ko_fast.cu + ko_fast.h): " + good + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("w") == 1234
+    assert bench.measured_traffic("other") is None
+    (csrc / "ko_fast.cu").write_text("kernel B")
+    assert bench.measured_traffic("w") is None
