@@ -376,6 +376,57 @@ void ko_model_destroy(ko_model *m);
 ko_status ko_eval_orders_noalloc(const ko_gpu *g, const int8_t *orders, int64_t n,
                                  int64_t *makespan_out, void *stream);
 
+/* ------------------------------------------------ hardware validation
+ * Sec. 6 measures launch orders by running them on the GPU.  These calls do
+ * that for synthetic busy kernels on the current device, so a kernel set's
+ * measured times can be ranked against its simulated makespans (the
+ * simulator's descriptor of this GPU and the kernels' per-block durations
+ * are calibrated by the caller from ko_hw_time_grid).
+ *
+ * A busy kernel (ko_hw_kernel, host memory):
+ *   kind     KO_HW_COMPUTE: every thread runs a dependent FMA chain of
+ *            `iters` steps; KO_HW_MEMORY: every thread streams `iters` 16-byte
+ *            loads from a 256 MB device buffer (addresses masked into it);
+ *   threads  block size, a multiple of 32 in [32, 1024];
+ *   smem     dynamic shared memory per block in bytes (reserved, not used;
+ *            it sets occupancy), up to the device's opt-in limit;
+ *   blocks   grid size in [1, 2^20];  iters  loop length in [0, 2^24].
+ * Both loops have a fixed length and wait on nothing. */
+#define KO_HW_COMPUTE 0
+#define KO_HW_MEMORY 1
+typedef struct {
+    int32_t kind, threads, smem, blocks, iters;
+} ko_hw_kernel;
+typedef struct ko_hw ko_hw;
+
+/* Copies n (1..8) kernel descriptions and creates n streams, events and the
+ * 256 MB buffer on the current device.  NULL on error (ko_last_error():
+ * KO_ERR_ARG for an invalid description, KO_ERR_NOMEM, KO_ERR_CUDA). */
+ko_hw *ko_hw_create(const ko_hw_kernel *ks, int32_t n);
+
+/* Limits of the current device as the simulator's GPU descriptor reads them:
+ * out[0] N_SM, [1] registers per SM, [2] shared memory per SM (bytes), [3]
+ * warps per SM, [4] resident blocks per SM, [5] shared memory the runtime
+ * reserves per block (bytes), [6] SM clock (kHz). */
+ko_status ko_hw_device_limits(int32_t out[7]);
+
+/* Registers per thread of the busy kernel of `kind` (cudaFuncGetAttributes). */
+ko_status ko_hw_regs(int32_t kind, int32_t *regs_per_thread);
+
+/* Times `count` launch orders (host, count x n kernel ids, row-major): for
+ * each order, `reps` runs (1..64) that launch kernel order[j] on stream j in
+ * host order j = 0..n-1 between a start event and a stop event that waits for
+ * every stream; ms_out[count] (host) gets the fastest run in milliseconds.
+ * KO_ERR_ARG if a row is not a permutation.  Synchronous. */
+ko_status ko_hw_time_orders(ko_hw *h, const int8_t *orders, int64_t count, int32_t reps, float *ms_out);
+
+/* Fastest of `reps` runs of kernel k alone with a grid of `blocks` blocks
+ * (calibration), in milliseconds.  Synchronous. */
+ko_status ko_hw_time_grid(ko_hw *h, int32_t k, int32_t blocks, int32_t reps, float *ms_out);
+
+/* Release streams, events and buffers.  NULL is ignored. */
+void ko_hw_destroy(ko_hw *h);
+
 /* Release the handle and its device scratch.  NULL is ignored. */
 void ko_destroy_gpu(ko_gpu *g);
 

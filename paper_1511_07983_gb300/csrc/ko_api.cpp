@@ -771,6 +771,49 @@ ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_
     return s ? fail(s) : ok();
 }
 
+ko_hw *ko_hw_create(const ko_hw_kernel *ks, int32_t n)
+{
+    ko_status err = KO_OK;
+    ko_hw *h = ko_hw_build(ks, n, &err);
+    if (!h) fail(err);
+    else ok();
+    return h;
+}
+
+ko_status ko_hw_device_limits(int32_t out[7])
+{
+    if (!out) return fail(KO_ERR_ARG);
+    ko_status s = ko_hw_limits_impl(out);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_hw_regs(int32_t kind, int32_t *regs_per_thread)
+{
+    if (!regs_per_thread || (kind != KO_HW_COMPUTE && kind != KO_HW_MEMORY)) return fail(KO_ERR_ARG);
+    int r = 0;
+    ko_status s = ko_hw_regs_impl(kind, &r);
+    if (s) return fail(s);
+    *regs_per_thread = r;
+    return ok();
+}
+
+ko_status ko_hw_time_orders(ko_hw *h, const int8_t *orders, int64_t count, int32_t reps, float *ms_out)
+{
+    if (!h || count < 0 || (count > 0 && (!orders || !ms_out)) || reps < 1 || reps > 64) return fail(KO_ERR_ARG);
+    ko_status s = ko_hw_time_impl(h, orders, count, reps, ms_out);
+    return s ? fail(s) : ok();
+}
+
+ko_status ko_hw_time_grid(ko_hw *h, int32_t k, int32_t blocks, int32_t reps, float *ms_out)
+{
+    if (!h || !ms_out || k < 0 || k >= 8 || blocks < 1 || blocks > (1 << 20) || reps < 1 || reps > 64)
+        return fail(KO_ERR_ARG);
+    ko_status s = ko_hw_time_grid_impl(h, k, blocks, reps, ms_out);
+    return s ? fail(s) : ok();
+}
+
+void ko_hw_destroy(ko_hw *h) { ko_hw_free(h); }
+
 ko_status ko_model_set_option(ko_model *m, int32_t key, int64_t value)
 {
     if (!m) return fail(KO_ERR_ARG);

@@ -101,6 +101,13 @@ size_t ko_noalloc_scratch_bytes();
 
 // Host-side Algorithm 1; returns the number of execution rounds.
 int ko_heuristic_host(const KoSet &h, int32_t *order_out, bool per_block = false);
+// Hardware validation (ko_hw.cu).
+ko_hw *ko_hw_build(const ko_hw_kernel *ks, int n, ko_status *err);
+void ko_hw_free(ko_hw *h);
+ko_status ko_hw_regs_impl(int kind, int *regs);
+ko_status ko_hw_limits_impl(int32_t *out);
+ko_status ko_hw_time_impl(ko_hw *h, const int8_t *orders, long long count, int reps, float *ms_out);
+ko_status ko_hw_time_grid_impl(ko_hw *h, int k, int blocks, int reps, float *ms_out);
 ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *start, bool moves, int max_iters,
                               int32_t *order_out, int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out,
                               double *gpu_ms, cudaStream_t st);

@@ -1,0 +1,169 @@
+"""Does the dispatch model rank launch orders the way this GPU does?
+
+Sec. 6 evaluates a launch order by running it on the hardware.  Here the same
+is done for sets of synthetic busy kernels (FMA-chain kernels of chosen block
+size, shared memory, grid and length, see ko_hw_create), every one of the N!
+orders timed on this GPU, and the times compared with the makespans the
+simulator gives for a descriptor of the same GPU:
+
+* GPU: N_SM, registers, shared memory, warps and resident blocks per SM as the
+  device reports them;
+* kernel i: registers per block = warps x (registers per thread x 32 rounded
+  up to 256, the per-warp allocation unit), shared memory per block = the
+  reserved amount + the dynamic amount, warps = threads / 32, N_tblk = grid;
+* c_i = the time of one block of kernel i running alone, in nanoseconds;
+  m_i = 1 (these kernels do not touch memory);
+* Ccap: either unbounded (durations are the alone times: the model is then
+  pure packing under the four SM limits and head-of-line blocking) or
+  calibrated from how much slower k co-resident blocks of the reference kernel
+  (the set's first) run than one (T(k) / T(1) = max(1, k c / Ccap) under the
+  duration rule).
+
+For each set the report gives Spearman's rank correlation between measured
+time and simulated makespan over all orders, the measured spread (worst /
+best), and where the simulator's best order and Algorithm 1's order land
+among the measured times.
+
+    python -m paper_1511_07983_gb300.hwval [--sets 8] [--n 6] [--json out.json]
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import math
+import time
+
+import numpy as np
+
+from . import ko
+from .synth import SplitMix64, _mix
+
+REG_UNIT = 256  # registers are allocated per warp in units of 256
+CAP_MAX = 1 << 30  # largest capacity the simulator takes; above 32 x the longest block it never binds
+
+
+def rankdata(x) -> np.ndarray:
+    """Ranks 1..n, ties given the mean of the ranks they span."""
+    x = np.asarray(x)
+    order = np.argsort(x, kind="mergesort")
+    xs = x[order]
+    ranks = np.empty(len(x), dtype=np.float64)
+    i = 0
+    while i < len(x):
+        j = i
+        while j + 1 < len(x) and xs[j + 1] == xs[i]:
+            j += 1
+        ranks[order[i:j + 1]] = (i + j) / 2.0 + 1.0
+        i = j + 1
+    return ranks
+
+
+def spearman(a, b) -> float:
+    """Pearson correlation of the two rank vectors."""
+    ra, rb = rankdata(a), rankdata(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = math.sqrt(float((ra * ra).sum()) * float((rb * rb).sum()))
+    return float((ra * rb).sum() / den) if den > 0 else float("nan")
+
+
+def draw_set(seed: int, n: int, n_sm: int, max_smem: int) -> list[tuple]:
+    """n busy-kernel shapes (threads, smem, blocks, target alone time in us)."""
+    rng = SplitMix64(_mix(0x48570000 + seed))
+    out = []
+    for _ in range(n):
+        threads = rng.choice([64, 128, 256, 512])
+        smem = rng.choice([0, 8 << 10, 24 << 10, 48 << 10, 96 << 10, 160 << 10])
+        smem = min(smem, max_smem)
+        blocks = rng.uniform_int(n_sm // 2, 4 * n_sm)
+        us = rng.uniform_int(20, 200)
+        out.append((threads, smem, blocks, us))
+    return out
+
+
+def model_kernel(threads, smem, blocks, c_ns, regs_per_thread, reserved):
+    warps = threads // 32
+    reg_warp = -(-regs_per_thread * 32 // REG_UNIT) * REG_UNIT
+    return (warps * reg_warp, smem + reserved, warps, blocks, max(1, int(c_ns)), 1)
+
+
+def calibrate_iters(target_us: float, base_iters: int, base_ms: float) -> int:
+    """Chain length for a target alone time, from a measured (iters, ms) pair."""
+    return max(1, min(1 << 24, int(round(base_iters * (target_us * 1e-3) / base_ms))))
+
+
+def run_set(seed: int, n: int, reps: int = 3) -> dict:
+    lim = ko.ko_hw_device_limits()
+    n_sm, regs_sm, smem_sm, warps_sm, blk_sm, reserved, _ = lim
+    regs = ko.ko_hw_regs(ko.KO_HW_COMPUTE)
+    shapes = draw_set(seed, n, n_sm, smem_sm - reserved)
+    # iterations per microsecond of the FMA chain, from one block of 128 threads
+    base_iters = 1 << 16
+    with ko.Hw([(ko.KO_HW_COMPUTE, 128, 0, 1, base_iters)]) as probe:
+        base_ms = probe.time_grid(0, 1, reps=5)
+    kernels = [(ko.KO_HW_COMPUTE, t, s, b, calibrate_iters(us, base_iters, base_ms)) for t, s, b, us in shapes]
+    with ko.Hw(kernels) as hw:
+        c_ns = [hw.time_grid(i, 1, reps=5) * 1e6 for i in range(n)]
+        # co-residence slowdown of the reference kernel (k blocks per SM where they fit)
+        t0, s0, _, _ = shapes[0]
+        fit = min(blk_sm, warps_sm // (t0 // 32), (smem_sm // (s0 + reserved)) if s0 + reserved > 0 else blk_sm,
+                  regs_sm // ((t0 // 32) * (-(-regs * 32 // REG_UNIT) * REG_UNIT)))
+        slow = []
+        t1 = hw.time_grid(0, n_sm, reps=5)
+        for k in range(1, max(1, fit) + 1):
+            slow.append((k, hw.time_grid(0, k * n_sm, reps=5) / t1))
+        # Ccap = c * k / slowdown at the most loaded point that is slowed down
+        k_max, sl = slow[-1]
+        ccap_cal = min(CAP_MAX, max(1, int(c_ns[0] * k_max / sl))) if sl > 1.05 else None
+        orders = np.array(list(itertools.permutations(range(n))), dtype=np.int8)
+        t_start = time.time()
+        measured = hw.time_orders(orders, reps=reps)
+        wall = time.time() - t_start
+    mk = [model_kernel(t, s, b, c, regs, reserved) for (t, s, b, _), c in zip(shapes, c_ns)]
+    out = {"seed": seed, "n": n, "shapes": shapes, "c_ns": c_ns, "regs_per_thread": regs,
+           "slowdown": slow, "timing_wall_s": wall,
+           "measured_ms": {"min": float(measured.min()), "max": float(measured.max()),
+                           "spread": float(measured.max() / measured.min())}}
+    for label, ccap in (("unbounded", CAP_MAX), ("calibrated", ccap_cal)):
+        if ccap is None:
+            out[label] = None
+            continue
+        with ko.Gpu(n_sm, regs_sm, smem_sm, warps_sm, blk_sm, c_cap=ccap, m_cap=CAP_MAX) as g:
+            for row in mk:
+                g.add_kernel(*row)
+            sim = np.asarray(g.eval_orders(orders=orders))
+            alg1 = g.heuristic_order().tolist()
+        best_sim = int(np.argmin(sim))
+        alg1_row = [i for i, o in enumerate(orders.tolist()) if o == alg1][0]
+        pct = lambda m: 100.0 * float((measured >= m).sum()) / len(measured)  # noqa: E731
+        out[label] = {"c_cap": ccap, "spearman": spearman(measured, sim),
+                      "sim_spread": float(sim.max() / sim.min()),
+                      "measured_percentile_of_sim_best": pct(measured[best_sim]),
+                      "measured_percentile_of_alg1": pct(measured[alg1_row]),
+                      "sim_best_measured_over_best": float(measured[best_sim] / measured.min())}
+    return out
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sets", type=int, default=8)
+    ap.add_argument("--n", type=int, default=6)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args(argv)
+    rows = []
+    for seed in range(a.sets):
+        r = run_set(seed, a.n, a.reps)
+        rows.append(r)
+        brief = {k: (None if r[k] is None else {kk: round(v, 4) if isinstance(v, float) else v
+                                                 for kk, v in r[k].items()})
+                 for k in ("unbounded", "calibrated")}
+        print(json.dumps({"seed": seed, "spread": round(r["measured_ms"]["spread"], 4), **brief}), flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(rows, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -98,6 +98,14 @@ _SIGNATURES = {
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "ko_hw_create": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "ko_hw_regs": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "ko_hw_device_limits": (ctypes.c_int32, [ctypes.c_void_p]),
+    "ko_hw_time_orders": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_void_p]),
+    "ko_hw_time_grid": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float)]),
+    "ko_hw_destroy": (None, [ctypes.c_void_p]),
     "ko_model_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -447,6 +455,67 @@ def ko_local_search(g, start=None, moves=True, max_iters=1 << 20, stream=None):
                                  _ptr(order), ctypes.byref(ms), ctypes.byref(steps), ctypes.byref(evals),
                                  ctypes.byref(t), _stream(stream)), "ko_local_search")
     return order[:n], ms.value, steps.value, evals.value, t.value
+
+
+KO_HW_COMPUTE, KO_HW_MEMORY = 0, 1
+
+
+class HwKernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("threads", ctypes.c_int32), ("smem", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("iters", ctypes.c_int32)]
+
+
+def ko_hw_device_limits():
+    """(N_SM, regs/SM, smem/SM, warps/SM, blocks/SM, reserved smem/block, SM kHz)."""
+    out = np.zeros(7, dtype=np.int32)
+    _check(lib().ko_hw_device_limits(_ptr(out)), "ko_hw_device_limits")
+    return tuple(int(v) for v in out)
+
+
+def ko_hw_regs(kind):
+    r = ctypes.c_int32()
+    _check(lib().ko_hw_regs(kind, ctypes.byref(r)), "ko_hw_regs")
+    return r.value
+
+
+class Hw:
+    """Busy kernels on the current GPU, timed alone or in launch orders."""
+
+    def __init__(self, kernels):
+        """kernels: sequence of (kind, threads, smem, blocks, iters)."""
+        arr = (HwKernel * len(kernels))(*[HwKernel(*map(int, k)) for k in kernels])
+        self.n = len(kernels)
+        self.h = lib().ko_hw_create(arr, self.n)
+        if not self.h:
+            raise KoError(lib().ko_last_error(), "ko_hw_create")
+
+    def time_orders(self, orders, reps=3):
+        o = np.ascontiguousarray(np.asarray(orders, dtype=np.int8).reshape(-1, self.n))
+        out = np.zeros(o.shape[0], dtype=np.float32)
+        _check(lib().ko_hw_time_orders(self.h, _ptr(o), o.shape[0], reps, _ptr(out)), "ko_hw_time_orders")
+        return out
+
+    def time_grid(self, k, blocks, reps=5):
+        t = ctypes.c_float()
+        _check(lib().ko_hw_time_grid(self.h, k, blocks, reps, ctypes.byref(t)), "ko_hw_time_grid")
+        return t.value
+
+    def close(self):
+        if self.h:
+            lib().ko_hw_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------ convenience

@@ -1,0 +1,42 @@
+"""Host-side pieces of the hardware validation (no GPU): the rank correlation
+against scipy's, tie handling, the model's per-block resource arithmetic and
+the seeded kernel shapes."""
+import numpy as np
+import pytest
+
+from paper_1511_07983_gb300 import hwval
+
+
+def test_spearman_matches_scipy():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        a = rng.integers(0, 12, 200)          # many ties
+        b = rng.normal(size=200) + 0.3 * a
+        assert hwval.spearman(a, b) == pytest.approx(stats.spearmanr(a, b).statistic, abs=1e-12)
+
+
+def test_rank_ties_take_mean_rank():
+    assert hwval.rankdata([10, 20, 20, 5]).tolist() == [2.0, 3.5, 3.5, 1.0]
+    assert hwval.spearman([1, 2, 3, 4], [10, 20, 30, 40]) == pytest.approx(1.0)
+    assert hwval.spearman([1, 2, 3, 4], [4, 3, 2, 1]) == pytest.approx(-1.0)
+
+
+def test_model_kernel_resources():
+    # 256 threads = 8 warps; 19 registers/thread -> 608 per warp, rounded to 768
+    assert hwval.model_kernel(256, 8192, 300, 12345.6, 19, 1024) == (8 * 768, 9216, 8, 300, 12345, 1)
+    assert hwval.model_kernel(64, 0, 1, 0.2, 8, 1024) == (2 * 256, 1024, 2, 1, 1, 1)
+
+
+def test_shapes_are_seeded_and_in_range():
+    a = hwval.draw_set(5, 6, 152, 200000)
+    assert a == hwval.draw_set(5, 6, 152, 200000)
+    assert a != hwval.draw_set(6, 6, 152, 200000)
+    for t, s, b, us in a:
+        assert t in (64, 128, 256, 512) and 0 <= s <= 200000 and 76 <= b <= 608 and 20 <= us <= 200
+
+
+def test_iteration_calibration():
+    assert hwval.calibrate_iters(100, 1 << 16, 0.2) == 32768
+    assert hwval.calibrate_iters(1e9, 1 << 16, 0.2) == 1 << 24
+    assert hwval.calibrate_iters(0, 1 << 16, 0.2) == 1
