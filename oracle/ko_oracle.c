@@ -12,6 +12,8 @@
  *                            orders (the "all permutations" space, Sec. 6).
  *   or_makespan              block-by-block dispatch simulation of one order
  *                            (Sec. 2 dispatch rule; duration rule = reading A1).
+ *   or_makespan_sampled      the same with durations fixed at placement instead
+ *                            of at the end of the burst (model variant).
  *   or_makespans_idx         many orders by Lehmer index, pthreads over ranges.
  *   or_heuristic             Algorithm 1 (ScoreGen, ProfileCombine, rounds);
  *   or_heuristic_fp          the same with a choice of footprint reading.
@@ -110,8 +112,14 @@ typedef struct {
 } resident_block;
 
 /* Makespan of launch order `order` (a permutation of 0..n-1).  Returns -1 if a
- * block cannot fit an empty SM (the simulation could never finish). */
-int64_t or_makespan(const or_gpu *g, int n, const or_kernel *k, const int32_t *order)
+ * block cannot fit an empty SM (the simulation could never finish).
+ *
+ * at_placement selects when a block's duration is fixed: 0 = after the burst
+ * that started it, with SumC/SumM over everything then resident on its SM
+ * (reading A2, or_makespan); 1 = the moment it is placed, with SumC/SumM over
+ * the blocks resident at that moment, itself included and blocks placed later
+ * in the same burst excluded (the alternative reading of the same passage). */
+int64_t or_makespan_sampled(const or_gpu *g, int n, const or_kernel *k, const int32_t *order, int at_placement)
 {
     const int64_t S = g->n_sm, Bk = g->n_blk_sm;
     for (int i = 0; i < n; i++) {
@@ -168,6 +176,11 @@ int64_t or_makespan(const or_gpu *g, int n, const or_kernel *k, const int32_t *o
             rb->kernel = i; rb->is_new = 1; rb->end = 0;
             used_r[s] += kk->n_reg; used_s[s] += kk->n_shm; used_w[s] += kk->n_warp; used_b[s]++;
             sum_c[s] += kk->c; sum_m[s] += kk->m;
+            if (at_placement) {
+                rb->end = t + duration(g, kk->c, kk->m, sum_c[s], sum_m[s]);
+                rb->is_new = 0;
+                if (rb->end > makespan) makespan = rb->end;
+            }
             p = (s + 1) % S;
             left--;
             while (pos < n && left == 0) { pos++; left = pos < n ? k[order[pos]].n_tblk : 0; }
@@ -200,6 +213,11 @@ int64_t or_makespan(const or_gpu *g, int n, const or_kernel *k, const int32_t *o
     free(used_r); free(used_s); free(used_w); free(used_b);
     free(sum_c); free(sum_m); free(res);
     return makespan;
+}
+
+int64_t or_makespan(const or_gpu *g, int n, const or_kernel *k, const int32_t *order)
+{
+    return or_makespan_sampled(g, n, k, order, 0);
 }
 
 /* ------------------------------------------------------ many orders, threads --- */
@@ -250,6 +268,12 @@ void or_makespans_orders(const or_gpu *g, int n, const or_kernel *k, const int32
                          int64_t count, int64_t *out)
 {
     for (int64_t j = 0; j < count; j++) out[j] = or_makespan(g, n, k, orders + j * n);
+}
+
+void or_makespans_orders_sampled(const or_gpu *g, int n, const or_kernel *k, const int32_t *orders,
+                                 int64_t count, int at_placement, int64_t *out)
+{
+    for (int64_t j = 0; j < count; j++) out[j] = or_makespan_sampled(g, n, k, orders + j * n, at_placement);
 }
 
 /* ------------------------------------------------------------- Algorithm 1 --- */

@@ -207,3 +207,41 @@ def test_table3_output_arithmetic():
         digits = 3 if dev < 0.1 else 2
         assert round(100 * out["deviation_from_optimal"], digits) == pytest.approx(dev, abs=1e-9), name
     assert math.factorial(8) == t3["orders"]["8 kernels"]
+
+
+# ------------------------------------------- duration sampled at placement ---
+
+def test_placement_sampling_hand_traced():
+    c = CASES["W1"]
+    orders = [o for o, _ in c["makespans_at_placement"]]
+    want = [m for _, m in c["makespans_at_placement"]]
+    assert oracle.makespans_sampled(c["gpu"], c["kernels"], orders, True).tolist() == want
+    assert oracle.makespans_sampled(c["gpu"], c["kernels"], orders, False).tolist() == \
+        [m for _, m in c["makespans"]]
+
+
+def test_placement_sampling_equals_burst_end_with_one_block_per_sm():
+    # one block slot per SM: the totals at placement are the totals after the burst
+    for seed in range(8):
+        s = synth.random_set(800 + seed, 5, gpu=(6, 65536, 49152, 64, 1), blk=(1, 20))
+        every = [list(p) for p in itertools.permutations(range(5))]
+        assert (oracle.makespans_sampled(s.gpu, s.kernels, every, True) ==
+                oracle.makespans_sampled(s.gpu, s.kernels, every, False)).all()
+
+
+def test_placement_sampling_equals_burst_end_when_capacity_never_binds():
+    # Ccap >= Bk * max c and Mcap >= Bk * max m: every duration is the alone time
+    for seed in range(8):
+        s = synth.random_set(810 + seed, 5, gpu=(6, 65536, 49152, 64, 8), blk=(4, 40), c=(1, 5000),
+                             c_cap=8 * 5000, m_cap=8 * 5000 * 10)
+        every = [list(p) for p in itertools.permutations(range(5))]
+        assert (oracle.makespans_sampled(s.gpu, s.kernels, every, True) ==
+                oracle.makespans_sampled(s.gpu, s.kernels, every, False)).all()
+
+
+def test_default_makespan_is_burst_end_sampling():
+    s = synth.gen_set("single8", 0)
+    idx = np.arange(0, 40320, 997, dtype=np.uint64)
+    orders = np.array([oracle.unrank(8, int(i)) for i in idx], dtype=np.int32)
+    assert (oracle.makespans_sampled(s.gpu, s.kernels, orders, False) ==
+            oracle.makespans_idx(s.gpu, s.kernels, idx)).all()
