@@ -98,6 +98,23 @@ ko_gpu *ko_create_gpu(int32_t n_sm, int32_t n_reg_sm, int32_t n_shm_sm, int32_t 
  * first evaluation. */
 ko_status ko_set_capacity(ko_gpu *g, int64_t c_cap, int64_t m_cap);
 
+/* When a started block's duration is fixed (the duration rule's SumC / SumM
+ * are sampled):
+ *   KO_SAMPLE_BURST_END     after the dispatch burst that started it, over
+ *                           everything then resident on its SM (default);
+ *   KO_SAMPLE_AT_PLACEMENT  when it is placed, over the blocks resident at
+ *                           that moment, itself included and blocks placed
+ *                           later in the same burst excluded.
+ * Sec. 2 and Sec. 4 do not say which; the second is a model variant for
+ * robustness checks of rankings.  It runs on the general simulator only:
+ * ko_eval_orders, ko_eval_all, ko_rank_order and ko_eval_orders_noalloc
+ * accept it; batches, the autotuner's fast path, local search and the
+ * surrogate calls return KO_ERR_ARG for such a handle.  KO_ERR_ARG for another
+ * value, KO_ERR_STATE after the first evaluation. */
+#define KO_SAMPLE_BURST_END 0
+#define KO_SAMPLE_AT_PLACEMENT 1
+ko_status ko_set_sampling(ko_gpu *g, int32_t mode);
+
 /* Append kernel i (Table 1, last three rows), all quantities per thread
  * block: n_reg_i = registers of one block (regs/thread x threads), n_shm_i =
  * shared-memory bytes of one block, n_warp_i = warps of one block,
@@ -423,6 +440,16 @@ ko_status ko_hw_time_orders(ko_hw *h, const int8_t *orders, int64_t count, int32
 /* Fastest of `reps` runs of kernel k alone with a grid of `blocks` blocks
  * (calibration), in milliseconds.  Synchronous. */
 ko_status ko_hw_time_grid(ko_hw *h, int32_t k, int32_t blocks, int32_t reps, float *ms_out);
+
+/* One run of one launch order (host, n ids) with every block traced.
+ * trace_out (host) receives 4 uint64 per block -- start and end time in ns of
+ * the device's global timer, SM id, kernel id -- kernels in id order, each
+ * kernel's blocks in index order: sum of the kernels' grids x 4 entries
+ * (ko_hw_trace_len).  The start is stamped by the block's first thread on
+ * entry, the end after all its threads are done.  *ms_out gets the run's
+ * event time.  Synchronous. */
+ko_status ko_hw_trace_order(ko_hw *h, const int8_t *order, uint64_t *trace_out, float *ms_out);
+int64_t ko_hw_trace_len(const ko_hw *h);
 
 /* Release streams, events and buffers.  NULL is ignored. */
 void ko_hw_destroy(ko_hw *h);

@@ -246,6 +246,14 @@ ko_status ko_set_capacity(ko_gpu *g, int64_t c_cap, int64_t m_cap)
     return ok();
 }
 
+ko_status ko_set_sampling(ko_gpu *g, int32_t mode)
+{
+    if (!g || (mode != KO_SAMPLE_BURST_END && mode != KO_SAMPLE_AT_PLACEMENT)) return fail(KO_ERR_ARG);
+    if (g->frozen) return fail(KO_ERR_STATE);
+    g->h.sampling = mode;
+    return ok();
+}
+
 int32_t ko_add_kernel(ko_gpu *g, int32_t n_reg_i, int32_t n_shm_i, int32_t n_warp_i,
                       int32_t n_tblk_i, int64_t c_i, int64_t m_i)
 {
@@ -626,7 +634,7 @@ ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
     std::vector<const KoSet *> hs(nsets);
     std::vector<int> levels(nsets);
     for (int i = 0; i < nsets; i++) {
-        if (!sets[i]) {
+        if (!sets[i] || sets[i]->h.sampling != KO_SAMPLE_BURST_END) {
             fail(KO_ERR_ARG);
             return nullptr;
         }
@@ -717,7 +725,7 @@ ko_status ko_surrogate_train(ko_model *m, ko_gpu *const *sets, int32_t nsets, in
     if (!m || !sets || nsets < 1) return fail(KO_ERR_ARG);
     std::vector<const KoSet *> hs(nsets);
     for (int i = 0; i < nsets; i++) {
-        if (!sets[i] || sets[i]->h.n < 1) return fail(KO_ERR_ARG);
+        if (!sets[i] || sets[i]->h.n < 1 || sets[i]->h.sampling != KO_SAMPLE_BURST_END) return fail(KO_ERR_ARG);
         sets[i]->frozen = true;
         hs[i] = &sets[i]->h;
     }
@@ -729,6 +737,7 @@ ko_status ko_surrogate_train(ko_model *m, ko_gpu *const *sets, int32_t nsets, in
 ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, uint64_t seed,
                                int32_t *best_order, int64_t *best_makespan, double *gpu_ms, void *stream)
 {
+    if (g && g->h.sampling != KO_SAMPLE_BURST_END) return fail(KO_ERR_ARG);
     if (!m || !g || !best_order || !best_makespan || g->h.n < 1) return fail(KO_ERR_ARG);
     g->frozen = true;
     ko_status s = ko_model_propose_set(m, g->h, n_cand, top_k, seed, best_order, best_makespan, gpu_ms,
@@ -740,6 +749,7 @@ ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t to
                               int32_t beam, uint64_t seed, int32_t *best_order, int64_t *best_makespan,
                               double *gpu_ms, void *stream)
 {
+    if (g && g->h.sampling != KO_SAMPLE_BURST_END) return fail(KO_ERR_ARG);
     if (!m || !g || !best_order || !best_makespan || g->h.n < 2) return fail(KO_ERR_ARG);
     g->frozen = true;
     ko_status s = ko_model_search_set(m, g->h, n_cand, top_k, rounds, beam, seed, best_order, best_makespan,
@@ -750,6 +760,7 @@ ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t to
 ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
                            int64_t *best_makespan, double *gpu_ms, void *stream)
 {
+    if (g && g->h.sampling != KO_SAMPLE_BURST_END) return fail(KO_ERR_ARG);
     if (!g || !best_order || !best_makespan || g->h.n < 1) return fail(KO_ERR_ARG);
     g->frozen = true;
     ko_status s = ko_random_search_set(&g->fast, g->h, n_orders, seed, best_order, best_makespan, gpu_ms,
@@ -761,6 +772,7 @@ ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_
                           int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out, double *gpu_ms,
                           void *stream)
 {
+    if (g && g->h.sampling != KO_SAMPLE_BURST_END) return fail(KO_ERR_ARG);
     if (!g || !order_out || !makespan_out || g->h.n < 1) return fail(KO_ERR_ARG);
     g->frozen = true;
     std::vector<int32_t> st0(g->h.n);
@@ -811,6 +823,15 @@ ko_status ko_hw_time_grid(ko_hw *h, int32_t k, int32_t blocks, int32_t reps, flo
     ko_status s = ko_hw_time_grid_impl(h, k, blocks, reps, ms_out);
     return s ? fail(s) : ok();
 }
+
+ko_status ko_hw_trace_order(ko_hw *h, const int8_t *order, uint64_t *trace_out, float *ms_out)
+{
+    if (!h || !order || !trace_out || !ms_out) return fail(KO_ERR_ARG);
+    ko_status s = ko_hw_trace_impl(h, order, (unsigned long long *)trace_out, ms_out);
+    return s ? fail(s) : ok();
+}
+
+int64_t ko_hw_trace_len(const ko_hw *h) { return h ? 4 * ko_hw_trace_blocks(h) : 0; }
 
 void ko_hw_destroy(ko_hw *h) { ko_hw_free(h); }
 

@@ -716,7 +716,7 @@ cudaError_t launch(const KoWork &a, cudaStream_t st)
 
 bool ko_fast_applicable(const KoSet &h)
 {
-    if (h.n < 1) return false;
+    if (h.n < 1 || h.sampling != KO_SAMPLE_BURST_END) return false;
     int64_t cmax = 0, mmax = 0;
     for (int i = 0; i < h.n; i++) {
         cmax = h.k[i].c > cmax ? h.k[i].c : cmax;

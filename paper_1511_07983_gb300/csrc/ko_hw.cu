@@ -25,18 +25,57 @@ namespace {
 constexpr size_t kBufBytes = 256ull << 20;  // power of two: indexes are masked into it
 constexpr int kMaxStreams = 8;
 
-__global__ void __launch_bounds__(1024) hw_compute_kernel(int iters, float b, float c, float *sink)
+__device__ __forceinline__ unsigned long long global_ns()
 {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Per-block trace record (4 words): start ns, end ns, SM id, kernel id.  Thread
+// 0 stamps the start on entry and the end after the block's last thread is done.
+struct Trace {
+    unsigned long long *rec;  // null: no tracing
+    int kid;
+    __device__ void begin() const
+    {
+        if (rec && threadIdx.x == 0) {
+            rec[4 * blockIdx.x + 0] = global_ns();
+            rec[4 * blockIdx.x + 2] = sm_id();
+            rec[4 * blockIdx.x + 3] = (unsigned long long)kid;
+        }
+    }
+    __device__ void end() const
+    {
+        if (rec) {
+            __syncthreads();
+            if (threadIdx.x == 0) rec[4 * blockIdx.x + 1] = global_ns();
+        }
+    }
+};
+
+__global__ void __launch_bounds__(1024) hw_compute_kernel(int iters, float b, float c, float *sink, Trace tr)
+{
+    tr.begin();
     float a = 1.0f + (float)threadIdx.x * 1e-3f;
 #pragma unroll 4
     for (int i = 0; i < iters; i++) a = fmaf(a, b, c);
     // never true for the values used (|a| stays finite and != -7.5); keeps the chain live
     if (a == -7.5f) sink[blockIdx.x] = a;
+    tr.end();
 }
 
 __global__ void __launch_bounds__(1024) hw_memory_kernel(const float4 *__restrict__ buf, unsigned long long mask,
-                                                         int iters, float *sink)
+                                                         int iters, float *sink, Trace tr)
 {
+    tr.begin();
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     float acc = 0.0f;
@@ -45,6 +84,7 @@ __global__ void __launch_bounds__(1024) hw_memory_kernel(const float4 *__restric
         acc += v.x + v.y + v.z + v.w;
     }
     if (acc == -7.5f) sink[blockIdx.x] = acc;
+    tr.end();
 }
 
 }  // namespace
@@ -55,6 +95,9 @@ struct ko_hw {
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done[kMaxStreams] = {};
     float4 *buf = nullptr;
     float *sink = nullptr;
+    unsigned long long *trace = nullptr;  // 4 words per block of every kernel, kernel k at trace_off[k]
+    std::vector<long long> trace_off;
+    long long trace_blocks = 0;
 };
 
 namespace {
@@ -70,17 +113,20 @@ void hw_free(ko_hw *h)
     if (h->ev_stop) cudaEventDestroy(h->ev_stop);
     cudaFree(h->buf);
     cudaFree(h->sink);
+    cudaFree(h->trace);
     delete h;
 }
 
-cudaError_t launch_one(ko_hw *h, int k, int blocks, cudaStream_t st)
+// blocks <= the kernel's grid when traced (the trace holds `blocks` records per kernel)
+cudaError_t launch_one(ko_hw *h, int k, int blocks, cudaStream_t st, bool traced = false)
 {
     const ko_hw_kernel &d = h->ks[k];
+    Trace tr{traced ? h->trace + 4 * h->trace_off[k] : nullptr, k};
     if (d.kind == KO_HW_COMPUTE)
-        hw_compute_kernel<<<blocks, d.threads, d.smem, st>>>(d.iters, 0.999999f, 1e-6f, h->sink);
+        hw_compute_kernel<<<blocks, d.threads, d.smem, st>>>(d.iters, 0.999999f, 1e-6f, h->sink, tr);
     else
         hw_memory_kernel<<<blocks, d.threads, d.smem, st>>>(h->buf, kBufBytes / sizeof(float4) - 1, d.iters,
-                                                            h->sink);
+                                                            h->sink, tr);
     ko_count_launch();
     return cudaGetLastError();
 }
@@ -106,6 +152,10 @@ ko_hw *ko_hw_build(const ko_hw_kernel *ks, int n, ko_status *err)
     ko_hw *h = new (std::nothrow) ko_hw();
     if (!h) { *err = KO_ERR_NOMEM; return nullptr; }
     h->ks.assign(ks, ks + n);
+    for (int i = 0; i < n; i++) {
+        h->trace_off.push_back(h->trace_blocks);
+        h->trace_blocks += ks[i].blocks;
+    }
     bool ok = cudaFuncSetAttribute(hw_compute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
                   cudaSuccess &&
               cudaFuncSetAttribute(hw_memory_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
@@ -115,7 +165,8 @@ ko_hw *ko_hw_build(const ko_hw_kernel *ks, int n, ko_status *err)
              cudaEventCreate(&h->ev_done[i]) == cudaSuccess;
     ok = ok && cudaEventCreate(&h->ev_start) == cudaSuccess && cudaEventCreate(&h->ev_stop) == cudaSuccess;
     if (!ok) { cudaGetLastError(); hw_free(h); *err = KO_ERR_CUDA; return nullptr; }
-    if (cudaMalloc((void **)&h->buf, kBufBytes) != cudaSuccess || cudaMalloc((void **)&h->sink, 1 << 22) != cudaSuccess) {
+    if (cudaMalloc((void **)&h->buf, kBufBytes) != cudaSuccess || cudaMalloc((void **)&h->sink, 1 << 22) != cudaSuccess ||
+        cudaMalloc((void **)&h->trace, sizeof(unsigned long long) * 4 * h->trace_blocks) != cudaSuccess) {
         cudaGetLastError();
         hw_free(h);
         *err = KO_ERR_NOMEM;
@@ -192,6 +243,40 @@ ko_status ko_hw_time_impl(ko_hw *h, const int8_t *orders, long long count, int r
     }
     return KO_OK;
 }
+
+// One run of one launch order with every block traced; records (host,
+// 4 words per block, kernels in id order, blocks in index order) and the
+// event time of the run.
+ko_status ko_hw_trace_impl(ko_hw *h, const int8_t *ord, unsigned long long *rec_out, float *ms_out)
+{
+    const int n = (int)h->ks.size();
+    unsigned used = 0;
+    for (int j = 0; j < n; j++) {
+        if (ord[j] < 0 || ord[j] >= n || ((used >> ord[j]) & 1u)) return KO_ERR_ARG;
+        used |= 1u << ord[j];
+    }
+    cudaStream_t s0 = h->streams[0];
+    const size_t bytes = sizeof(unsigned long long) * 4 * h->trace_blocks;
+    if (cudaMemsetAsync(h->trace, 0, bytes, s0) != cudaSuccess || cudaStreamSynchronize(s0) != cudaSuccess)
+        return KO_ERR_CUDA;
+    if (cudaEventRecord(h->ev_start, s0) != cudaSuccess) return KO_ERR_CUDA;
+    for (int j = 1; j < n; j++)
+        if (cudaStreamWaitEvent(h->streams[j], h->ev_start, 0) != cudaSuccess) return KO_ERR_CUDA;
+    for (int j = 0; j < n; j++)
+        if (launch_one(h, ord[j], h->ks[ord[j]].blocks, h->streams[j], true) != cudaSuccess) return KO_ERR_CUDA;
+    for (int j = 1; j < n; j++) {
+        if (cudaEventRecord(h->ev_done[j], h->streams[j]) != cudaSuccess ||
+            cudaStreamWaitEvent(s0, h->ev_done[j], 0) != cudaSuccess)
+            return KO_ERR_CUDA;
+    }
+    if (cudaEventRecord(h->ev_stop, s0) != cudaSuccess || cudaEventSynchronize(h->ev_stop) != cudaSuccess ||
+        cudaEventElapsedTime(ms_out, h->ev_start, h->ev_stop) != cudaSuccess)
+        return KO_ERR_CUDA;
+    if (cudaMemcpy(rec_out, h->trace, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return KO_ERR_CUDA;
+    return KO_OK;
+}
+
+long long ko_hw_trace_blocks(const ko_hw *h) { return h->trace_blocks; }
 
 // One kernel alone with a chosen grid (calibration of per-block durations and
 // of the co-residence slowdown); the fastest of `reps` runs.

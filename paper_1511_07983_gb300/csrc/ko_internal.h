@@ -20,6 +20,8 @@ struct KoSet {
     int32_t S, R, Sh, W, Bk;     // N_SM and the four per-SM limits
     int64_t ccap, mcap;          // compute / memory capacity (R_B = ccap / mcap)
     int32_t cshift, mshift;      // log2(capacity) when a power of two, else -1
+    int32_t sampling;            // KO_SAMPLE_BURST_END or KO_SAMPLE_AT_PLACEMENT
+    int32_t pad0;
     int64_t ref_makespan;        // makespan the exhaustive counts compare against
     KoKern k[KO_MAX_KERNELS];
 };
@@ -108,6 +110,8 @@ ko_status ko_hw_regs_impl(int kind, int *regs);
 ko_status ko_hw_limits_impl(int32_t *out);
 ko_status ko_hw_time_impl(ko_hw *h, const int8_t *orders, long long count, int reps, float *ms_out);
 ko_status ko_hw_time_grid_impl(ko_hw *h, int k, int blocks, int reps, float *ms_out);
+ko_status ko_hw_trace_impl(ko_hw *h, const int8_t *ord, unsigned long long *rec_out, float *ms_out);
+long long ko_hw_trace_blocks(const ko_hw *h);
 ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *start, bool moves, int max_iters,
                               int32_t *order_out, int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out,
                               double *gpu_ms, cudaStream_t st);

@@ -144,16 +144,29 @@ __device__ int64_t simulate(const KoSet &d, const int8_t *perm, Slab st)
             }
             if (found < 0) break;
             const int s = found;
-            int g = st.ng[s], j = 0;
-            while (j < g && (st.gk[s * G + j] & 0xffff) != (kid | kPending)) j++;
-            if (j == g) {
-                st.gk[s * G + g] = kid | kPending;
-                st.gend[s * G + g] = 0;
-                st.ng[s] = g + 1;
-            }
-            st.gk[s * G + j] += 1 << 16;
             st.ur[s] += K.r; st.us[s] += K.s; st.uw[s] += K.w; st.ub[s] += 1;
             st.sum_c[s] += K.c; st.sum_m[s] += K.m;
+            int g = st.ng[s], j = 0;
+            if (d.sampling == KO_SAMPLE_AT_PLACEMENT) {
+                // duration fixed now, from the totals with this block and without later ones;
+                // blocks of one kernel ending together share a group
+                const int64_t e = t + block_duration(d, K.c, K.m, st.sum_c[s], st.sum_m[s]);
+                while (j < g && !((st.gk[s * G + j] & 0xffff) == kid && st.gend[s * G + j] == e)) j++;
+                if (j == g) {
+                    st.gk[s * G + g] = kid;
+                    st.gend[s * G + g] = e;
+                    st.ng[s] = g + 1;
+                }
+                if (e > makespan) makespan = e;
+            } else {
+                while (j < g && (st.gk[s * G + j] & 0xffff) != (kid | kPending)) j++;
+                if (j == g) {
+                    st.gk[s * G + g] = kid | kPending;
+                    st.gend[s * G + g] = 0;
+                    st.ng[s] = g + 1;
+                }
+            }
+            st.gk[s * G + j] += 1 << 16;
             p = (s + 1 == S) ? 0 : s + 1;
             if (--left == 0) {
                 pos++;

@@ -21,8 +21,10 @@ simulator gives for a descriptor of the same GPU:
 
 For each set the report gives Spearman's rank correlation between measured
 time and simulated makespan over all orders, the measured spread (worst /
-best), and where the simulator's best order and Algorithm 1's order land
-among the measured times.
+best), where the simulator's best order and Algorithm 1's order land among
+the measured times, and, from per-block traces of two orders, how often the
+hardware starts a block of a later-issued kernel before the earlier kernel's
+last block (the model's first-in-first-out premise, Sec. 2).
 
     python -m paper_1511_07983_gb300.hwval [--sets 8] [--n 6] [--json out.json]
 """
@@ -45,18 +47,9 @@ CAP_MAX = 1 << 30  # largest capacity the simulator takes; above 32 x the longes
 
 def rankdata(x) -> np.ndarray:
     """Ranks 1..n, ties given the mean of the ranks they span."""
-    x = np.asarray(x)
-    order = np.argsort(x, kind="mergesort")
-    xs = x[order]
-    ranks = np.empty(len(x), dtype=np.float64)
-    i = 0
-    while i < len(x):
-        j = i
-        while j + 1 < len(x) and xs[j + 1] == xs[i]:
-            j += 1
-        ranks[order[i:j + 1]] = (i + j) / 2.0 + 1.0
-        i = j + 1
-    return ranks
+    _, inv, cnt = np.unique(np.asarray(x), return_inverse=True, return_counts=True)
+    last = np.cumsum(cnt).astype(np.float64)
+    return ((last - cnt + 1.0 + last) / 2.0)[inv.reshape(-1)]
 
 
 def spearman(a, b) -> float:
@@ -80,6 +73,33 @@ def draw_set(seed: int, n: int, n_sm: int, max_smem: int) -> list[tuple]:
         us = rng.uniform_int(20, 200)
         out.append((threads, smem, blocks, us))
     return out
+
+
+def dispatch_order_stats(rec: np.ndarray, order) -> dict:
+    """How far one traced run departs from the model's dispatch premise (Sec. 2:
+    every block of an earlier-issued kernel is dispatched before any block of a
+    later one).  rec: [blocks, 4] records (start ns, end ns, SM, kernel id).
+
+    * overtaken: fraction of blocks, over kernels issued second and later,
+      that started before the last block of the kernel issued just before;
+    * inversions: fraction of block pairs from different kernels whose start
+      times are in the opposite order of their kernels' issue positions;
+    * first_start_us: each kernel's first block start after the run's first,
+      in issue order."""
+    t0 = rec[:, 0].astype(np.int64)
+    kid = rec[:, 3].astype(np.int64)
+    base = int(t0.min())
+    starts = [np.sort(t0[kid == k]) for k in order]
+    later = sum(len(x) for x in starts[1:])
+    overtaken = sum(int((starts[j] < starts[j - 1][-1]).sum()) for j in range(1, len(order)))
+    inv = pairs = 0
+    for i in range(len(order)):
+        for j in range(i + 1, len(order)):
+            # pairs (a of position i, b of position j) with b starting strictly before a
+            inv += int(np.searchsorted(starts[j], starts[i], side="left").sum())
+            pairs += len(starts[i]) * len(starts[j])
+    return {"overtaken": overtaken / later if later else 0.0, "inversions": inv / pairs if pairs else 0.0,
+            "first_start_us": [round((int(x[0]) - base) / 1e3, 3) for x in starts]}
 
 
 def model_kernel(threads, smem, blocks, c_ns, regs_per_thread, reserved):
@@ -120,9 +140,13 @@ def run_set(seed: int, n: int, reps: int = 3) -> dict:
         t_start = time.time()
         measured = hw.time_orders(orders, reps=reps)
         wall = time.time() - t_start
+        traced = {}
+        for name, o in (("identity", list(range(n))), ("reversed", list(range(n))[::-1])):
+            rec, _ = hw.trace_order(o)
+            traced[name] = dispatch_order_stats(rec, o)
     mk = [model_kernel(t, s, b, c, regs, reserved) for (t, s, b, _), c in zip(shapes, c_ns)]
     out = {"seed": seed, "n": n, "shapes": shapes, "c_ns": c_ns, "regs_per_thread": regs,
-           "slowdown": slow, "timing_wall_s": wall,
+           "slowdown": slow, "timing_wall_s": wall, "dispatch": traced,
            "measured_ms": {"min": float(measured.min()), "max": float(measured.max()),
                            "spread": float(measured.max() / measured.min())}}
     for label, ccap in (("unbounded", CAP_MAX), ("calibrated", ccap_cal)):
@@ -159,7 +183,8 @@ def main(argv=None) -> None:
         brief = {k: (None if r[k] is None else {kk: round(v, 4) if isinstance(v, float) else v
                                                  for kk, v in r[k].items()})
                  for k in ("unbounded", "calibrated")}
-        print(json.dumps({"seed": seed, "spread": round(r["measured_ms"]["spread"], 4), **brief}), flush=True)
+        print(json.dumps({"seed": seed, "spread": round(r["measured_ms"]["spread"], 4), **brief,
+                          "dispatch": r["dispatch"]}), flush=True)
     if a.json:
         with open(a.json, "w") as f:
             json.dump(rows, f, indent=1)

@@ -105,7 +105,11 @@ _SIGNATURES = {
                                            ctypes.c_void_p]),
     "ko_hw_time_grid": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float)]),
+    "ko_hw_trace_order": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_float)]),
+    "ko_hw_trace_len": (ctypes.c_int64, [ctypes.c_void_p]),
     "ko_hw_destroy": (None, [ctypes.c_void_p]),
+    "ko_set_sampling": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     "ko_model_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -200,6 +204,13 @@ def ko_heuristic_order(g):
     out = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().ko_heuristic_order(g, _ptr(out)), "ko_heuristic_order")
     return out[:n]
+
+
+KO_SAMPLE_BURST_END, KO_SAMPLE_AT_PLACEMENT = 0, 1
+
+
+def ko_set_sampling(g, mode):
+    return _check(lib().ko_set_sampling(g, mode), "ko_set_sampling")
 
 
 KO_HEUR_PER_SM = 0
@@ -495,6 +506,15 @@ class Hw:
         _check(lib().ko_hw_time_orders(self.h, _ptr(o), o.shape[0], reps, _ptr(out)), "ko_hw_time_orders")
         return out
 
+    def trace_order(self, order):
+        """Per-block records [blocks, 4] (start ns, end ns, SM, kernel) of one
+        run of `order`, and the run's event time in ms."""
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int8).reshape(self.n))
+        rec = np.zeros(lib().ko_hw_trace_len(self.h), dtype=np.uint64)
+        t = ctypes.c_float()
+        _check(lib().ko_hw_trace_order(self.h, _ptr(o), _ptr(rec), ctypes.byref(t)), "ko_hw_trace_order")
+        return rec.reshape(-1, 4), t.value
+
     def time_grid(self, k, blocks, reps=5):
         t = ctypes.c_float()
         _check(lib().ko_hw_time_grid(self.h, k, blocks, reps, ctypes.byref(t)), "ko_hw_time_grid")
@@ -529,9 +549,11 @@ class Gpu:
             ko_set_capacity(self.h, c_cap, m_cap)
 
     @classmethod
-    def from_set(cls, kset):
+    def from_set(cls, kset, sampling=KO_SAMPLE_BURST_END):
         """Handle for a synth.KernelSet (gpu 7-tuple + int64 [N, 6] kernels)."""
         g = cls(*kset.gpu[:5], c_cap=kset.gpu[5], m_cap=kset.gpu[6])
+        if sampling != KO_SAMPLE_BURST_END:
+            ko_set_sampling(g.h, sampling)
         for row in np.asarray(kset.kernels).tolist():
             g.add_kernel(*row)
         return g

@@ -64,6 +64,10 @@ def test_argument_validation(ko):
     assert ko.ko_status_str(-3) == "KO_ERR_TOO_LARGE"
     with pytest.raises(ko.KoError):
         ko.ko_set_capacity(g.h, 0, 1)
+    with pytest.raises(ko.KoError):
+        ko.ko_set_sampling(g.h, 2)
+    ko.ko_set_sampling(g.h, ko.KO_SAMPLE_AT_PLACEMENT)
+    ko.ko_set_sampling(g.h, ko.KO_SAMPLE_BURST_END)
 
 
 def _sets():

@@ -63,3 +63,20 @@ def test_small_validation_run(ko):
         if r[k] is not None:
             assert -1.0 <= r[k]["spearman"] <= 1.0 or math.isnan(r[k]["spearman"])
             assert 0 < r[k]["measured_percentile_of_sim_best"] <= 100
+
+
+def test_trace_records(ko):
+    n_sm = ko.ko_hw_device_limits()[0]
+    ks = [(ko.KO_HW_COMPUTE, 128, 0, 300, 1 << 12), (ko.KO_HW_COMPUTE, 256, 16 << 10, 50, 1 << 12),
+          (ko.KO_HW_MEMORY, 128, 0, 200, 16)]
+    with ko.Hw(ks) as hw:
+        rec, ms = hw.trace_order([2, 0, 1])
+        assert rec.shape == (550, 4) and ms > 0
+        assert (rec[:, 0] > 0).all() and (rec[:, 1] >= rec[:, 0]).all()
+        assert (rec[:, 2] < n_sm).all()
+        assert rec[:, 3].tolist() == [0] * 300 + [1] * 50 + [2] * 200
+        # every block ran inside the timed interval (global timer in ns, events in ms)
+        span_ms = (int(rec[:, 1].max()) - int(rec[:, 0].min())) / 1e6
+        assert 0 < span_ms <= ms * 1.05 + 0.05
+        with pytest.raises(ko.KoError):
+            hw.trace_order([0, 0, 1])

@@ -40,3 +40,17 @@ def test_iteration_calibration():
     assert hwval.calibrate_iters(100, 1 << 16, 0.2) == 32768
     assert hwval.calibrate_iters(1e9, 1 << 16, 0.2) == 1 << 24
     assert hwval.calibrate_iters(0, 1 << 16, 0.2) == 1
+
+
+def test_dispatch_stats_on_synthetic_traces():
+    # strict FIFO: kernel 1's blocks start after kernel 0's last start
+    rec = np.array([[0, 9, 0, 0], [10, 19, 1, 0], [20, 29, 0, 1], [30, 39, 1, 1]], dtype=np.uint64)
+    s = hwval.dispatch_order_stats(rec, [0, 1])
+    assert s["overtaken"] == 0.0 and s["inversions"] == 0.0 and s["first_start_us"] == [0.0, 0.02]
+    # issued as [1, 0]: both of kernel 0's blocks start... kernel 0 is second here
+    s = hwval.dispatch_order_stats(rec, [1, 0])
+    assert s["overtaken"] == 1.0 and s["inversions"] == 1.0
+    # one of kernel 1's two blocks overtakes kernel 0's last block
+    rec2 = np.array([[0, 9, 0, 0], [30, 39, 1, 0], [20, 29, 0, 1], [40, 49, 1, 1]], dtype=np.uint64)
+    s = hwval.dispatch_order_stats(rec2, [0, 1])
+    assert s["overtaken"] == 0.5 and s["inversions"] == 0.25
