@@ -370,8 +370,9 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
     rescores its top_k exactly and then runs `rounds` of network-ranked local
     search around a beam of the best exact orders (ko_surrogate_search); plain
     search simulates as many uniform orders as fit in the surrogate's measured
-    GPU time.  Both best makespans are
-    ranked against the exact makespans of ref_orders seeded uniform orders."""
+    GPU time.  Exact local search from Algorithm 1's order (ko_local_search,
+    swaps and moves, its own time) is reported beside them.  The best makespans
+    are ranked against the exact makespans of ref_orders seeded uniform orders."""
     import numpy as np
     from paper_1511_07983_gb300 import ko, synth
     t0 = time.perf_counter()
@@ -396,10 +397,14 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
             n_plain = max(1, int((1 << 16) * s_ms / max(cal_ms, 1e-3)))
             _, p_best, p_ms = ko.ko_random_search(g, n_plain, seed=seed + 100 + j)
             h_ms = int(g.eval_orders(orders=np.array([g.heuristic_order()], dtype=np.int8))[0])
+            _, l_best, _, l_orders, l_ms = g.local_search(moves=True)
             rows.append({"n": ks.n, "n_sm": ks.gpu[0], "surrogate_ms": s_ms, "plain_ms": p_ms,
-                         "plain_orders": n_plain,
+                         "plain_orders": n_plain, "local_search_ms": l_ms, "local_search_orders": l_orders,
+                         "makespans": {"surrogate": int(s_best), "plain": int(p_best), "local_search": int(l_best),
+                                       "heuristic": h_ms},
                          "surrogate_pct": percentile_of(s_best, ref),
                          "plain_pct": percentile_of(p_best, ref),
+                         "local_search_pct": percentile_of(l_best, ref),
                          "heuristic_pct": percentile_of(h_ms, ref)})
     model.close()
     mean = lambda k: sum(r[k] for r in rows) / len(rows)
@@ -412,6 +417,13 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
             "heuristic_percentile_mean": mean("heuristic_pct"),
             "surrogate_wins": sum(r["surrogate_pct"] > r["plain_pct"] for r in rows),
             "ties": sum(r["surrogate_pct"] == r["plain_pct"] for r in rows),
+            # exact steepest descent from Algorithm 1 (swaps + moves): no model, its own time
+            "local_search_percentile_mean": mean("local_search_pct"),
+            "local_search_ms_mean": mean("local_search_ms"),
+            "surrogate_vs_local_search_makespan": {
+                "lower": sum(r["makespans"]["surrogate"] < r["makespans"]["local_search"] for r in rows),
+                "equal": sum(r["makespans"]["surrogate"] == r["makespans"]["local_search"] for r in rows),
+                "higher": sum(r["makespans"]["surrogate"] > r["makespans"]["local_search"] for r in rows)},
             "per_set": rows}
 
 

@@ -176,7 +176,7 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 
 /* Tuning knobs of the device simulators (set by the tuner; per handle).
  *   KO_OPT_LANES        lanes that share one simulation in the run-length
- *                       simulator: 16 or 32 (default 32)
+ *                       simulator: 16 or 32 (default 16)
  *   KO_OPT_LEVELS       prefix-sharing depth: exhaustive work items fix the
  *                       first N-1-levels kernels and walk the rest depth
  *                       first, saving `levels` states; 0..6 (default 4)

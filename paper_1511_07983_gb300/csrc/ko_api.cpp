@@ -604,7 +604,7 @@ ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream)
     ko_status s = prepare(g, st);
     if (s) return fail(s);
     if ((s = upload_meta(g, st))) return fail(s);
-    int lanes = 32, levels = 4;
+    int lanes = 16, levels = 4;
     double rate = 0.0;
     s = ko_tune_set(&g->fast, g->h, g->d_set, g->d_acc, cache_path, st, &lanes, &levels, &rate);
     if (s) return fail(s);

@@ -50,7 +50,7 @@ struct KoFastState {
     void *fb_scratch = nullptr; // fallback slabs
     size_t fb_bytes = 0;
     unsigned long long last_overflow = 0;
-    int lanes = 32;             // lanes per simulation (16 or 32)
+    int lanes = 16;             // lanes per simulation (16 or 32)
     int levels = 4;             // saved DFS levels (items fix N - 1 - levels kernels)
     bool disabled = false;      // use the simple simulator only
     int run_limit = 32;         // cap on runs per simulation (tests force the hand-over)

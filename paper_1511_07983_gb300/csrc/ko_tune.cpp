@@ -17,7 +17,7 @@
 namespace {
 
 struct Choice {
-    int lanes = 32, levels = 4;
+    int lanes = 16, levels = 4;
     double rate = 0.0;
 };
 
