@@ -74,6 +74,8 @@ def lib():
             L.or_makespans_orders_sampled.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64),
                                                       P(ctypes.c_int32), ctypes.c_int64, ctypes.c_int,
                                                       P(ctypes.c_int64)]
+            L.or_makespans_ps.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32),
+                                          ctypes.c_int64, P(ctypes.c_double)]
             L.or_heuristic.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32)]
             L.or_heuristic.restype = ctypes.c_int
             L.or_heuristic_fp.argtypes = [P(_Gpu), ctypes.c_int, P(ctypes.c_int64), ctypes.c_int,
@@ -168,6 +170,21 @@ def makespans_sampled(gpu, kernels, orders, at_placement: bool) -> np.ndarray:
         lib().or_makespans_orders_sampled(ctypes.byref(g), k.shape[0], _p(k, ctypes.c_int64),
                                           _p(o, ctypes.c_int32), o.shape[0], int(bool(at_placement)),
                                           _p(out, ctypes.c_int64))
+    return out
+
+
+def makespans_ps(gpu, kernels, orders) -> np.ndarray:
+    """Makespans (float64) of explicit orders under processor sharing with
+    rates re-evaluated at every event (model variant)."""
+    k = _kern(kernels)
+    g = _gpu(gpu)
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32))
+    if o.ndim == 1:
+        o = o.reshape(1, -1)
+    out = np.empty(o.shape[0], dtype=np.float64)
+    if o.shape[0]:
+        lib().or_makespans_ps(ctypes.byref(g), k.shape[0], _p(k, ctypes.c_int64), _p(o, ctypes.c_int32),
+                              o.shape[0], _p(out, ctypes.c_double))
     return out
 
 

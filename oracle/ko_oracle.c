@@ -14,6 +14,8 @@
  *                            (Sec. 2 dispatch rule; duration rule = reading A1).
  *   or_makespan_sampled      the same with durations fixed at placement instead
  *                            of at the end of the burst (model variant).
+ *   or_makespan_ps           processor sharing: rates re-evaluated at every
+ *                            event (model variant, double precision).
  *   or_makespans_idx         many orders by Lehmer index, pthreads over ranges.
  *   or_heuristic             Algorithm 1 (ScoreGen, ProfileCombine, rounds);
  *   or_heuristic_fp          the same with a choice of footprint reading.
@@ -274,6 +276,147 @@ void or_makespans_orders_sampled(const or_gpu *g, int n, const or_kernel *k, con
                                  int64_t count, int at_placement, int64_t *out)
 {
     for (int64_t j = 0; j < count; j++) out[j] = or_makespan_sampled(g, n, k, orders + j * n, at_placement);
+}
+
+/* ------------------------------------------------- processor sharing --- */
+/*
+ * Model variant: processor sharing with rates re-evaluated at every event.
+ * Dispatch is the same FIFO round-robin first fit (Sec. 2).  A resident block
+ * has remaining compute work Rc (c at start) and memory work Rm (m at start);
+ * on an SM whose resident demands sum to SumC and SumM, every block progresses
+ * at rate rc = Ccap / max(SumC, Ccap) on Rc and rm = Mcap / max(SumM, Mcap) on
+ * Rm, and it ends when both reach zero: at t + max(Rc / rc, Rm / rm) if the
+ * rates stay.  When an SM's residents change (a release or a placement at
+ * time t), its other blocks are first advanced to t at the old rates, then
+ * their ends are recomputed at the new rates.  With residents that never
+ * change this is the duration rule of reading A1 without the rounding up.
+ * Times are doubles, every operation written out in a fixed order (compiled
+ * without contraction) so that another implementation with the same order
+ * gets the same bits; groups whose end equals the event time leave together.
+ * Returns -1 if a block cannot fit an empty SM.
+ */
+typedef struct {
+    int32_t kernel, fresh;
+    int64_t cnt;
+    double rc_left, rm_left, t_upd, end;
+} ps_group;
+
+static double ps_rate(int64_t sum, int64_t cap)
+{
+    return sum <= cap ? 1.0 : (double)cap / (double)sum;
+}
+
+double or_makespan_ps(const or_gpu *g, int n, const or_kernel *k, const int32_t *order)
+{
+    const int64_t S = g->n_sm, Bk = g->n_blk_sm;
+    for (int i = 0; i < n; i++)
+        if (k[i].n_reg > g->n_reg_sm || k[i].n_shm > g->n_shm_sm || k[i].n_warp > g->n_warp_sm)
+            return -1.0;
+    int64_t *ur = calloc((size_t)S, sizeof(int64_t)), *us = calloc((size_t)S, sizeof(int64_t));
+    int64_t *uw = calloc((size_t)S, sizeof(int64_t)), *ub = calloc((size_t)S, sizeof(int64_t));
+    int64_t *sc = calloc((size_t)S, sizeof(int64_t)), *sm = calloc((size_t)S, sizeof(int64_t));
+    double *rate_c = malloc(sizeof(double) * (size_t)S), *rate_m = malloc(sizeof(double) * (size_t)S);
+    int *ng = calloc((size_t)S, sizeof(int)), *changed = calloc((size_t)S, sizeof(int));
+    ps_group *gr = calloc((size_t)(S * Bk), sizeof(ps_group));
+    for (int64_t s = 0; s < S; s++) { rate_c[s] = 1.0; rate_m[s] = 1.0; }
+
+    double t = 0.0, makespan = 0.0;
+    int64_t p = 0;
+    int pos = 0;
+    int64_t left = n > 0 ? k[order[0]].n_tblk : 0;
+    while (pos < n && left == 0) { pos++; left = pos < n ? k[order[pos]].n_tblk : 0; }
+    for (;;) {
+        /* release every group whose end is t */
+        for (int64_t s = 0; s < S; s++) {
+            changed[s] = 0;
+            for (int j = 0; j < ng[s];) {
+                ps_group *q = &gr[s * Bk + j];
+                if (q->end == t) {
+                    const or_kernel *kk = &k[q->kernel];
+                    ur[s] -= q->cnt * kk->n_reg; us[s] -= q->cnt * kk->n_shm; uw[s] -= q->cnt * kk->n_warp;
+                    ub[s] -= q->cnt; sc[s] -= q->cnt * kk->c; sm[s] -= q->cnt * kk->m;
+                    gr[s * Bk + j] = gr[s * Bk + ng[s] - 1];
+                    ng[s]--;
+                    changed[s] = 1;
+                } else {
+                    j++;
+                }
+            }
+        }
+        /* one dispatch burst: FIFO, round-robin first fit from p */
+        while (pos < n) {
+            const int i = order[pos];
+            const or_kernel *kk = &k[i];
+            int64_t f = -1;
+            for (int64_t off = 0; off < S; off++) {
+                int64_t s = (p + off) % S;
+                if (ur[s] + kk->n_reg <= g->n_reg_sm && us[s] + kk->n_shm <= g->n_shm_sm &&
+                    uw[s] + kk->n_warp <= g->n_warp_sm && ub[s] + 1 <= Bk) {
+                    f = s;
+                    break;
+                }
+            }
+            if (f < 0) break;
+            int j = 0;
+            while (j < ng[f] && !(gr[f * Bk + j].fresh && gr[f * Bk + j].kernel == i)) j++;
+            if (j == ng[f]) {
+                ps_group *q = &gr[f * Bk + j];
+                q->kernel = i; q->fresh = 1; q->cnt = 0;
+                q->rc_left = (double)kk->c; q->rm_left = (double)kk->m; q->t_upd = t; q->end = 0.0;
+                ng[f]++;
+            }
+            gr[f * Bk + j].cnt++;
+            ur[f] += kk->n_reg; us[f] += kk->n_shm; uw[f] += kk->n_warp; ub[f]++;
+            sc[f] += kk->c; sm[f] += kk->m;
+            changed[f] = 1;
+            p = (f + 1) % S;
+            left--;
+            while (pos < n && left == 0) { pos++; left = pos < n ? k[order[pos]].n_tblk : 0; }
+        }
+        /* advance the changed SMs' blocks to t at the old rates, re-time them at the new */
+        for (int64_t s = 0; s < S; s++) {
+            if (!changed[s]) continue;
+            const double nrc = ps_rate(sc[s], g->c_cap), nrm = ps_rate(sm[s], g->m_cap);
+            for (int j = 0; j < ng[s]; j++) {
+                ps_group *q = &gr[s * Bk + j];
+                if (!q->fresh) {
+                    const double dt = t - q->t_upd;
+                    double a = rate_c[s] * dt;
+                    q->rc_left = q->rc_left - a;
+                    if (q->rc_left < 0.0) q->rc_left = 0.0;
+                    a = rate_m[s] * dt;
+                    q->rm_left = q->rm_left - a;
+                    if (q->rm_left < 0.0) q->rm_left = 0.0;
+                    q->t_upd = t;
+                }
+                q->fresh = 0;
+                const double tc = q->rc_left / nrc, tm = q->rm_left / nrm;
+                q->end = t + (tc > tm ? tc : tm);
+            }
+            rate_c[s] = nrc;
+            rate_m[s] = nrm;
+        }
+        /* next event */
+        double tmin = -1.0;
+        for (int64_t s = 0; s < S; s++)
+            for (int j = 0; j < ng[s]; j++)
+                if (tmin < 0.0 || gr[s * Bk + j].end < tmin) tmin = gr[s * Bk + j].end;
+        if (tmin < 0.0) {
+            if (pos < n) makespan = -1.0;
+            break;
+        }
+        t = tmin;
+        makespan = t;
+    }
+    free(ur); free(us); free(uw); free(ub); free(sc); free(sm);
+    free(rate_c); free(rate_m); free(ng); free(changed); free(gr);
+    return makespan;
+}
+
+void or_makespans_ps(const or_gpu *g, int n, const or_kernel *k, const int32_t *orders, int64_t count,
+                     double *out)
+{
+    for (int64_t j = 0; j < count; j++) out[j] = or_makespan_ps(g, n, k, orders + j * n);
 }
 
 /* ------------------------------------------------------------- Algorithm 1 --- */

@@ -56,7 +56,7 @@ def test_unrank_endpoints(n):
 
 # ---------------------------------------------------------- hand traces ---
 
-@pytest.mark.parametrize("name", ["W1", "T3", "T4", "W2"])
+@pytest.mark.parametrize("name", ["W1", "T3", "T4", "W2", "P1", "P2"])
 def test_hand_traced_makespans(name):
     c = CASES[name]
     for order, expect in c["makespans"]:
@@ -245,3 +245,32 @@ def test_default_makespan_is_burst_end_sampling():
     orders = np.array([oracle.unrank(8, int(i)) for i in idx], dtype=np.int32)
     assert (oracle.makespans_sampled(s.gpu, s.kernels, orders, False) ==
             oracle.makespans_idx(s.gpu, s.kernels, idx)).all()
+
+
+# ------------------------------------------------------ processor sharing ---
+
+@pytest.mark.parametrize("name", ["P1", "P2"])
+def test_processor_sharing_hand_traced(name):
+    c = CASES[name]
+    orders = [o for o, _ in c["makespans_ps"]]
+    got = oracle.makespans_ps(c["gpu"], c["kernels"], orders)
+    for g, (_, want) in zip(got.tolist(), c["makespans_ps"]):
+        assert g == pytest.approx(want, rel=1e-12)
+
+
+def test_processor_sharing_equals_duration_rule_when_capacity_never_binds():
+    for seed in range(8):
+        s = synth.random_set(820 + seed, 5, gpu=(6, 65536, 49152, 64, 8), blk=(4, 40), c=(1, 5000),
+                            c_cap=8 * 5000, m_cap=8 * 5000 * 10)
+        every = [list(p) for p in itertools.permutations(range(5))]
+        assert (oracle.makespans_ps(s.gpu, s.kernels, every) ==
+                oracle.makespans_sampled(s.gpu, s.kernels, every, False).astype(np.float64)).all()
+
+
+def test_processor_sharing_one_wave_closed_form():
+    # 16 identical blocks, 4 per SM, all start at 0 and end together at c * SumC / Ccap
+    gpu = (4, 65536, 49152, 64, 4, 1500, 1 << 30)
+    kern = [[1024, 0, 2, 16, 1000, 1]]
+    assert oracle.makespans_ps(gpu, kern, [[0]])[0] == pytest.approx(1000 * 4000 / 1500, rel=1e-15)
+    # the duration rule rounds the same end up
+    assert oracle.makespan(gpu, kern, [0]) == math.ceil(1000 * 4000 / 1500)
