@@ -26,14 +26,27 @@ def test_model_kernel_resources():
     # 256 threads = 8 warps; 19 registers/thread -> 608 per warp, rounded to 768
     assert hwval.model_kernel(256, 8192, 300, 12345.6, 19, 1024) == (8 * 768, 9216, 8, 300, 12345, 1)
     assert hwval.model_kernel(64, 0, 1, 0.2, 8, 1024) == (2 * 256, 1024, 2, 1, 1, 1)
+    assert hwval.model_kernel(64, 0, 1, 7.9, 8, 1024, m_ns=790.2) == (512, 1024, 2, 1, 7, 790)
 
 
 def test_shapes_are_seeded_and_in_range():
     a = hwval.draw_set(5, 6, 152, 200000)
     assert a == hwval.draw_set(5, 6, 152, 200000)
     assert a != hwval.draw_set(6, 6, 152, 200000)
-    for t, s, b, us in a:
+    for kind, t, s, b, us in a:
+        assert kind == 0
         assert t in (64, 128, 256, 512) and 0 <= s <= 200000 and 76 <= b <= 608 and 20 <= us <= 200
+    m = hwval.draw_set(5, 6, 152, 200000, mixed=True)
+    kinds = [x[0] for x in m]
+    assert sorted(set(kinds)) == [0, 1] and all(kinds[i] != kinds[i + 1] for i in range(5))
+
+
+def test_blocks_that_fit():
+    lim = (152, 65536, 233472, 64, 32, 1024, 0)
+    assert hwval.blocks_that_fit(128, 0, 16, lim) == 16          # warps: 64 / 4
+    assert hwval.blocks_that_fit(64, 96 << 10, 16, lim) == 2      # shared memory
+    assert hwval.blocks_that_fit(32, 0, 255, lim) == 8            # registers: 65536 / 8192
+    assert hwval.blocks_that_fit(1024, 0, 64, lim) == 1
 
 
 def test_iteration_calibration():
