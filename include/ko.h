@@ -161,6 +161,18 @@ ko_status ko_heuristic_order_ex(ko_gpu *g, int32_t reading, int32_t *order_out);
 ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
                          int64_t *makespan_out, void *stream);
 
+/* Makespans of n explicit orders (n x N kernel ids, host or device) under the
+ * processor-sharing model variant: the same dispatch (Sec. 2), but every
+ * resident block progresses its remaining compute and memory work at the rates
+ * its SM's current totals allow, Ccap / max(SumC, Ccap) and
+ * Mcap / max(SumM, Mcap), re-evaluated whenever the SM's residents change; a
+ * block ends when both are done.  With residents that never change this is the
+ * duration rule without rounding up.  Times are doubles computed in a fixed
+ * operation order without contraction.  makespan_out[n] (host or device)
+ * receives them, -1 for a row that is not a permutation.  Ignores
+ * ko_set_sampling.  Synchronises `stream` when a buffer is on the host. */
+ko_status ko_eval_orders_ps(ko_gpu *g, const int8_t *orders, int64_t n, double *makespan_out, void *stream);
+
 /* Exhaustive scoring of all N! orders (N <= 12, else KO_ERR_TOO_LARGE) and the
  * rank of one order among them.  `order` (host, N ids) is ranked; NULL ranks
  * the Algorithm 1 order.  If hist != NULL (host or device, nbins >= 1

@@ -297,6 +297,52 @@ ko_status ko_heuristic_order(ko_gpu *g, int32_t *order_out)
     return ok();
 }
 
+ko_status ko_eval_orders_ps(ko_gpu *g, const int8_t *orders, int64_t n, double *makespan_out, void *stream)
+{
+    if (!g || n < 0 || (n > 0 && (!orders || !makespan_out))) return fail(KO_ERR_ARG);
+    if (n == 0) return ok();
+    const int N = g->h.n;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool out_dev = is_device_ptr(makespan_out);
+    if (N == 0) {
+        if (out_dev) {
+            if (cudaMemsetAsync(makespan_out, 0, sizeof(double) * n, st) != cudaSuccess) return fail(KO_ERR_CUDA);
+        } else {
+            std::memset(makespan_out, 0, sizeof(double) * n);
+        }
+        return ok();
+    }
+    ko_status s = prepare(g, st);
+    if (s) return fail(s);
+    const size_t in_bytes = (size_t)n * N;
+    const bool in_dev = is_device_ptr(orders);
+    const size_t need = (in_dev ? 0 : (in_bytes + 255) / 256 * 256) + (out_dev ? 0 : sizeof(double) * n);
+    if ((s = grow(&g->d_stage, &g->stage_cap, std::max<size_t>(need, 256)))) return fail(s);
+    char *stage = (char *)g->d_stage;
+    const int8_t *d_in = orders;
+    if (!in_dev) {
+        if (cudaMemcpyAsync(stage, orders, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+        g->h2d += (long long)in_bytes;
+        d_in = (const int8_t *)stage;
+        stage += (in_bytes + 255) / 256 * 256;
+    }
+    double *d_out = out_dev ? makespan_out : (double *)stage;
+    const size_t per = ko_ps_scratch_per_thread(g->h);
+    size_t slots = std::max<size_t>(128, std::min<size_t>(kSimpleScratchBudget / per, 152 * 8 * 128));
+    slots = std::max<size_t>(128, std::min<size_t>(slots, (size_t)((n + 127) / 128) * 128));
+    if ((s = grow(&g->scratch, &g->scratch_bytes, slots * per))) return fail(s);
+    if ((s = check_cuda(ko_launch_ps(g->d_set, g->h, d_in, n, d_out, g->scratch, g->scratch_bytes, st))))
+        return fail(s);
+    if (!out_dev) {
+        if (cudaMemcpyAsync(makespan_out, d_out, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail(KO_ERR_CUDA);
+        g->d2h += (long long)sizeof(double) * n;
+    }
+    if ((!in_dev || !out_dev) && cudaStreamSynchronize(st) != cudaSuccess) return fail(KO_ERR_CUDA);
+    return ok();
+}
+
 ko_status ko_heuristic_order_ex(ko_gpu *g, int32_t reading, int32_t *order_out)
 {
     if (!g || (!order_out && g->h.n > 0) || (reading != KO_HEUR_PER_SM && reading != KO_HEUR_PER_BLOCK))

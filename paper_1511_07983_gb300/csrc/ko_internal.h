@@ -39,6 +39,12 @@ void ko_count_launch(int n = 1);
 // ------------------------------------------------------------------ launchers
 // All launchers are asynchronous on `stream` and return the launch status.
 
+// Processor-sharing simulator (ko_sim_ps.cu): makespans (double) of explicit
+// rows (N bytes each), per-thread scratch of ko_ps_scratch_per_thread bytes.
+size_t ko_ps_scratch_per_thread(const KoSet &h);
+cudaError_t ko_launch_ps(const KoSet *d_set, const KoSet &h_set, const int8_t *perms, int64_t count, double *out,
+                         void *scratch, size_t scratch_bytes, cudaStream_t stream);
+
 // Per-thread scratch bytes the simple simulator needs for one set.
 size_t ko_simple_scratch_per_thread(const KoSet &h);
 

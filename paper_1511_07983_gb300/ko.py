@@ -110,6 +110,8 @@ _SIGNATURES = {
     "ko_hw_trace_len": (ctypes.c_int64, [ctypes.c_void_p]),
     "ko_hw_destroy": (None, [ctypes.c_void_p]),
     "ko_set_sampling": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
+    "ko_eval_orders_ps": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
     "ko_model_set_option": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "ko_model_destroy": (None, [ctypes.c_void_p]),
     "ko_eval_orders_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -211,6 +213,18 @@ KO_SAMPLE_BURST_END, KO_SAMPLE_AT_PLACEMENT = 0, 1
 
 def ko_set_sampling(g, mode):
     return _check(lib().ko_set_sampling(g, mode), "ko_set_sampling")
+
+
+def ko_eval_orders_ps(g, orders, out=None, stream=None):
+    """Processor-sharing makespans (float64) of rows of kernel ids (int8);
+    numpy (host) or torch CUDA tensors."""
+    if isinstance(orders, np.ndarray) or not hasattr(orders, "data_ptr"):
+        orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int8))
+    n = orders.shape[0]
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    _check(lib().ko_eval_orders_ps(g, _ptr(orders), n, _ptr(out), _stream(stream)), "ko_eval_orders_ps")
+    return out
 
 
 KO_HEUR_PER_SM = 0
@@ -572,6 +586,9 @@ class Gpu:
         if reading == KO_HEUR_PER_SM:
             return ko_heuristic_order(self.h)
         return ko_heuristic_order_ex(self.h, reading)
+
+    def eval_orders_ps(self, orders, out=None, stream=None):
+        return ko_eval_orders_ps(self.h, orders, out=out, stream=stream)
 
     def local_search(self, start=None, moves=True, max_iters=1 << 20, stream=None):
         return ko_local_search(self, start=start, moves=moves, max_iters=max_iters, stream=stream)

@@ -9,12 +9,12 @@ strategies are Algorithm 1 under the two readings of its resource terms
 search (swaps, or swaps and moves) started from Algorithm 1's order or from
 the order the kernels were added in.
 
-With --sampling K it also compares, on K ten-kernel sets, the two readings of
-when a block's duration is fixed (after its burst, the default, or at its
-placement): rank agreement over all orders and how each reading's best order
-and Algorithm 1's order rank under the other.
+With --variants K it also compares, on K ten-kernel sets, the default model
+with its two variants (durations fixed at placement; processor sharing with
+rates re-evaluated at every event): rank agreement over all orders and how
+each model's best order and Algorithm 1's order rank under the other.
 
-    python -m paper_1511_07983_gb300.study [--sets10 64] [--n11 16] [--sampling 16] [--json out.json]
+    python -m paper_1511_07983_gb300.study [--sets10 64] [--n11 16] [--variants 16] [--json out.json]
 """
 from __future__ import annotations
 
@@ -59,31 +59,44 @@ def rank_set(s) -> dict:
     return out
 
 
-def sampling_set(s) -> dict:
-    """The same set under both duration-sampling readings (burst end, the
-    default; placement time, the variant): rank agreement over all N! orders
-    and how each reading's optimum and Algorithm 1's order fare under the
-    other."""
+def variants_set(s) -> dict:
+    """One set under the default model (durations fixed after each burst) and
+    its two variants -- durations fixed at placement, and processor sharing
+    with rates re-evaluated at every event: for each variant, rank agreement
+    with the default over all N! orders, the share of orders whose makespan
+    changes, how each model's optimum ranks under the other, and Algorithm 1's
+    percentile under both."""
+    import itertools
     import torch
     from .hwval import spearman
     n = s.n
-    ms = {}
-    for name, mode in (("burst_end", ko.KO_SAMPLE_BURST_END), ("at_placement", ko.KO_SAMPLE_AT_PLACEMENT)):
-        with ko.Gpu.from_set(s, sampling=mode) as g:
-            every = torch.empty(math.factorial(n), dtype=torch.int64, device="cuda")
-            g.eval_all(every)
-            torch.cuda.synchronize()
-            ms[name] = every.cpu().numpy()
-            alg1 = g.heuristic_order()
-    a, b = ms["burst_end"], ms["at_placement"]
-    idx_alg1 = int(sum(int(d) * math.factorial(n - 1 - j) for j, d in enumerate(_lehmer_digits(alg1))))
+    with ko.Gpu.from_set(s) as g:
+        every = torch.empty(math.factorial(n), dtype=torch.int64, device="cuda")
+        g.eval_all(every)
+        torch.cuda.synchronize()
+        base = every.cpu().numpy()
+        alg1 = g.heuristic_order()
+    with ko.Gpu.from_set(s, sampling=ko.KO_SAMPLE_AT_PLACEMENT) as g:
+        every = torch.empty(math.factorial(n), dtype=torch.int64, device="cuda")
+        g.eval_all(every)
+        torch.cuda.synchronize()
+        placement = every.cpu().numpy()
+    rows = torch.tensor(list(itertools.permutations(range(n))), dtype=torch.int8, device="cuda")
+    with ko.Gpu.from_set(s) as g:
+        ps = torch.empty(rows.shape[0], dtype=torch.float64, device="cuda")
+        g.eval_orders_ps(rows, out=ps)
+        torch.cuda.synchronize()
+        ps = ps.cpu().numpy()
+    del rows
+    ia = int(sum(int(d) * math.factorial(n - 1 - j) for j, d in enumerate(_lehmer_digits(alg1))))
     pct = lambda v, m: 100.0 * float((v >= m).sum()) / len(v)  # noqa: E731
-    return {"n": n, "n_sm": int(s.gpu[0]), "spearman": spearman(a, b),
-            "changed_orders": float((a != b).mean()),
-            "burst_end_optimum_percentile_at_placement": pct(b, b[int(np.argmin(a))]),
-            "at_placement_optimum_percentile_burst_end": pct(a, a[int(np.argmin(b))]),
-            "alg1_percentile_burst_end": pct(a, a[idx_alg1]),
-            "alg1_percentile_at_placement": pct(b, b[idx_alg1])}
+    out = {"n": n, "n_sm": int(s.gpu[0]), "alg1_percentile_burst_end": pct(base, base[ia])}
+    for name, v in (("at_placement", placement), ("processor_sharing", ps)):
+        out[name] = {"spearman": spearman(base, v), "changed_orders": float((base != v).mean()),
+                     "burst_end_optimum_percentile": pct(v, v[int(np.argmin(base))]),
+                     "optimum_percentile_burst_end": pct(base, base[int(np.argmin(v))]),
+                     "alg1_percentile": pct(v, v[ia])}
+    return out
 
 
 def _lehmer_digits(order):
@@ -114,8 +127,8 @@ def main(argv=None) -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--sets10", type=int, default=64, help="N=10 sets on the 15-SM GPU")
     ap.add_argument("--n11", type=int, default=16, help="N=11 sets on the 148-SM GPU")
-    ap.add_argument("--sampling", type=int, default=0,
-                    help="also compare the two duration-sampling readings on this many N=10 sets")
+    ap.add_argument("--variants", type=int, default=0,
+                    help="also compare the model with its two variants on this many N=10 sets")
     ap.add_argument("--json", default=None)
     a = ap.parse_args(argv)
     groups = {"sets10 (N=10, 15 SMs)": [synth.gen_set("sets10", i) for i in range(a.sets10)],
@@ -128,14 +141,15 @@ def main(argv=None) -> None:
         rows = [rank_set(s) for s in sets]
         report[name] = {"summary": summarise(rows), "wall_s": time.time() - t0, "sets": rows}
         print(json.dumps({name: report[name]["summary"]}, indent=1), flush=True)
-    if a.sampling:
+    if a.variants:
         t0 = time.time()
-        rows = [sampling_set(synth.gen_set("sets10", i)) for i in range(a.sampling)]
-        keys = [k for k in rows[0] if k not in ("n", "n_sm")]
-        summ = {k: float(np.mean([r[k] for r in rows])) for k in keys}
-        summ["min_spearman"] = float(min(r["spearman"] for r in rows))
-        report["sampling readings, sets10"] = {"summary": summ, "wall_s": time.time() - t0, "sets": rows}
-        print(json.dumps({"sampling readings, sets10": summ}, indent=1), flush=True)
+        rows = [variants_set(synth.gen_set("sets10", i)) for i in range(a.variants)]
+        summ = {"alg1_percentile_burst_end": float(np.mean([r["alg1_percentile_burst_end"] for r in rows]))}
+        for name in ("at_placement", "processor_sharing"):
+            summ[name] = {k: float(np.mean([r[name][k] for r in rows])) for k in rows[0][name]}
+            summ[name]["min_spearman"] = float(min(r[name]["spearman"] for r in rows))
+        report["model variants, sets10"] = {"summary": summ, "wall_s": time.time() - t0, "sets": rows}
+        print(json.dumps({"model variants, sets10": summ}, indent=1), flush=True)
     if a.json:
         with open(a.json, "w") as f:
             json.dump(report, f, indent=1)

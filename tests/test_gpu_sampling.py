@@ -85,18 +85,21 @@ def test_calls_that_need_the_default_reading(ko):
             ko.ko_set_sampling(g.h, ko.KO_SAMPLE_BURST_END)   # after the first evaluation
 
 
-def test_sampling_study_matches_oracle(ko):
+def test_variants_study_matches_oracle(ko):
     import itertools
     from paper_1511_07983_gb300 import hwval, study
     s = synth.gen_set("single8", 0)
-    r = study.sampling_set(s)
+    r = study.variants_set(s)
     every = np.array(list(itertools.permutations(range(8))), dtype=np.int32)   # lexicographic
     a = oracle.makespans_sampled(s.gpu, s.kernels, every, False)
-    b = oracle.makespans_sampled(s.gpu, s.kernels, every, True)
-    assert r["changed_orders"] == pytest.approx(float((a != b).mean()), abs=1e-15)
-    assert r["spearman"] == pytest.approx(hwval.spearman(a, b), abs=1e-12)
     h = oracle.heuristic(s.gpu, s.kernels)
     ih = [i for i, p in enumerate(every.tolist()) if p == h][0]
-    assert r["alg1_percentile_at_placement"] == pytest.approx(100.0 * (b >= b[ih]).sum() / b.size, abs=1e-12)
-    assert r["burst_end_optimum_percentile_at_placement"] == pytest.approx(
-        100.0 * (b >= b[int(np.argmin(a))]).sum() / b.size, abs=1e-12)
+    assert r["alg1_percentile_burst_end"] == pytest.approx(100.0 * (a >= a[ih]).sum() / a.size, abs=1e-12)
+    for name, b in (("at_placement", oracle.makespans_sampled(s.gpu, s.kernels, every, True)),
+                    ("processor_sharing", oracle.makespans_ps(s.gpu, s.kernels, every))):
+        v = r[name]
+        assert v["changed_orders"] == pytest.approx(float((a != b).mean()), abs=1e-15)
+        assert v["spearman"] == pytest.approx(hwval.spearman(a, b), abs=1e-12)
+        assert v["alg1_percentile"] == pytest.approx(100.0 * (b >= b[ih]).sum() / b.size, abs=1e-12)
+        assert v["burst_end_optimum_percentile"] == pytest.approx(
+            100.0 * (b >= b[int(np.argmin(a))]).sum() / b.size, abs=1e-12)
