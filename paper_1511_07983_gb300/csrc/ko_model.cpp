@@ -79,6 +79,7 @@ struct ko_model {
     int *pick = nullptr;
     KoFastState fast{};
     int tc_forward = 1;        // inference layers on tcgen05 (1) or mma.sync (0)
+    int chunk = 262144;        // candidate rows per forward pass of the proposal paths
     int *tc_err = nullptr;     // device flag: a tcgen05 completion wait gave up
 
     void free_acts()
@@ -123,6 +124,18 @@ ko_status cuda_ok(cudaError_t e)
     if (e == cudaSuccess) return KO_OK;
     cudaGetLastError();
     return KO_ERR_CUDA;
+}
+
+// Two timing events; both null on failure.
+static ko_status make_events(cudaEvent_t *e0, cudaEvent_t *e1)
+{
+    if (cudaEventCreate(e0) != cudaSuccess || cudaEventCreate(e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (*e0) cudaEventDestroy(*e0);
+        *e0 = *e1 = nullptr;
+        return KO_ERR_CUDA;
+    }
+    return KO_OK;
 }
 
 ko_status refresh_bf16(ko_model *md, cudaStream_t st)
@@ -269,10 +282,18 @@ void ko_model_free(ko_model *md) { delete md; }
 
 ko_status ko_model_option(ko_model *md, int key, long long value)
 {
-    if (key != 1 || (value != 0 && value != 1)) return KO_ERR_ARG;
-    md->tc_forward = (int)value;
-    if (cudaMemset(md->tc_err, 0, sizeof(int)) != cudaSuccess) return KO_ERR_CUDA;
-    return KO_OK;
+    if (key == KO_MODEL_OPT_TC) {
+        if (value != 0 && value != 1) return KO_ERR_ARG;
+        md->tc_forward = (int)value;
+        if (cudaMemset(md->tc_err, 0, sizeof(int)) != cudaSuccess) return KO_ERR_CUDA;
+        return KO_OK;
+    }
+    if (key == KO_MODEL_OPT_CHUNK) {
+        if (value < 1024 || value > (1 << 22) || value % 1024) return KO_ERR_ARG;
+        md->chunk = (int)value;
+        return KO_OK;
+    }
+    return KO_ERR_ARG;
 }
 
 // KO_ERR_TIMEOUT if a tcgen05 layer reported that its completion wait gave up.
@@ -460,7 +481,7 @@ ko_status ko_model_propose_set(ko_model *md, const KoSet &h, long long n_cand, i
     SetTables tb;
     ko_status s = build_tables(hs, 1, &tb, st);
     if (s) return s;
-    const int C = 65536;
+    const int C = md->chunk;
     const long long padded = (n_cand + C - 1) / C * C;
     int8_t *rows = nullptr, *top_rows = nullptr;
     float *y_all = nullptr;
@@ -475,11 +496,8 @@ ko_status ko_model_propose_set(ko_model *md, const KoSet &h, long long n_cand, i
         s = KO_ERR_NOMEM;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (!s) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        s = ensure_acts(md, C);
-    }
+    if (!s) s = make_events(&e0, &e1);
+    if (!s) s = ensure_acts(md, C);
     if (!s) {
         cudaEventRecord(e0, st);
         if (cudaMemsetAsync(rows, 0, (size_t)padded * kMaxK, st) != cudaSuccess) s = KO_ERR_CUDA;
@@ -538,7 +556,7 @@ ko_status ko_model_search_set(ko_model *md, const KoSet &h, long long n_cand, in
     SetTables tb;
     ko_status s = build_tables(hs, 1, &tb, st);
     if (s) return s;
-    const int C = 65536;
+    const int C = md->chunk;
     const int k2 = 256;
     const long long padded = (n_cand + C - 1) / C * C;
     const int per = n * (n - 1) / 2 + n * (n - 1);
@@ -583,11 +601,8 @@ ko_status ko_model_search_set(ko_model *md, const KoSet &h, long long n_cand, in
         pool.swap(kept);
         return KO_OK;
     };
-    if (!s) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        s = ensure_acts(md, C);
-    }
+    if (!s) s = make_events(&e0, &e1);
+    if (!s) s = ensure_acts(md, C);
     if (!s) {
         cudaEventRecord(e0, st);
         // screening
@@ -665,9 +680,8 @@ ko_status ko_random_search_set(KoFastState *fs, const KoSet &h, long long n_orde
     if (!dalloc(&rows, (size_t)n_orders * kMaxK) || !dalloc(&ms, (size_t)n_orders) || !dalloc(&d_chunk, 1))
         s = KO_ERR_NOMEM;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!s) s = make_events(&e0, &e1);
     if (!s) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
         s = cuda_ok(ko_mlp_random_orders(rows, kMaxK, n_orders, h.n, mix64(seed ^ 0xBEEFull), st));
         if (!s) s = exact_rows(fs, tb.sets, h, 0, rows, n_orders, ms, d_chunk, st);
@@ -730,9 +744,8 @@ ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *st
     int64_t cur_ms = -1, evals = 0;
     int steps = 0;
     std::vector<int64_t> hm((size_t)(nq > 0 ? nq : 1));
+    if (!s) s = make_events(&e0, &e1);
     if (!s) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
         if (cudaMemcpyAsync(base, cur.data(), kMaxK, cudaMemcpyHostToDevice, st) != cudaSuccess) s = KO_ERR_CUDA;
         if (!s) s = exact_rows(fs, tb.sets, h, 0, base, 1, ms + per, d_chunk, st);

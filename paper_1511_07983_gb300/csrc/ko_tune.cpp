@@ -159,9 +159,13 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
     w.levels = n - 1 - d0 > 0 ? n - 1 - d0 : 1;
     const int saved_lanes = fs->lanes;
     fs->lanes = lanes;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        fs->lanes = saved_lanes;
+        return 0.0;
+    }
     double rate = 0.0;
     for (int rep = 0; rep < reps; rep++) {
         if (ko_launch_accum_reset(d_acc, 1, st) != cudaSuccess) break;

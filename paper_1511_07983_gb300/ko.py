@@ -383,6 +383,10 @@ class Model:
         """Inference layers on tcgen05 (True) or warp-level mma.sync (False)."""
         _check(lib().ko_model_set_option(self.m, 1, int(bool(on))), "ko_model_set_option")
 
+    def set_chunk(self, rows: int):
+        """Candidate rows per forward pass of propose/search (multiple of 1024)."""
+        _check(lib().ko_model_set_option(self.m, 2, int(rows)), "ko_model_set_option")
+
     def get_params(self):
         out = np.empty(KO_MODEL_PARAMS, dtype=np.float32)
         _check(lib().ko_model_get_params(self.m, _ptr(out)), "ko_model_get_params")

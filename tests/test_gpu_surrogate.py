@@ -158,3 +158,20 @@ def test_tcgen05_forward_matches_mma_and_oracle(ko):
     with ko.Gpu.from_set(s) as g:
         order, ms, _ = m.search(g, n_cand=65536, top_k=128, rounds=2, beam=4, seed=1)
     assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
+
+
+def test_chunk_size_does_not_change_results(ko):
+    s = synth.gen_set("large", 3)
+    m = ko.Model(seed=9)
+    out = []
+    with ko.Gpu.from_set(s) as g:
+        for rows in (65536, 1 << 18, 3 * 1024):
+            m.set_chunk(rows)
+            o1, ms1, _ = m.propose(g, n_cand=200000, top_k=256, seed=4)
+            o2, ms2, _ = m.search(g, n_cand=100000, top_k=128, rounds=2, beam=4, seed=5)
+            out.append((o1.tolist(), ms1, o2.tolist(), ms2))
+        for bad in (1000, 0, 1 << 23):
+            with pytest.raises(ko.KoError):
+                m.set_chunk(bad)
+    m.close()
+    assert out[0] == out[1] == out[2]
