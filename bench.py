@@ -14,7 +14,8 @@ the launching stream, barrier + synchronize on both sides, max over ranks).
 `e2e` times the same call with host output buffers (device->host copies of the
 histogram and results inside the timed region).  `--impl reference` times the
 CPU oracle on this machine's cores on a bounded sample of the same workload.
-Multi-GPU runs are independent replicas (one per rank); see the design doc.
+Multi-GPU runs are independent replicas (one per rank): every rank scores the
+whole space; only a barrier and the maximum of the per-rank times cross ranks.
 """
 from __future__ import annotations
 

@@ -280,7 +280,8 @@ void ko_batch_destroy(ko_batch *b);
  * small MLP predicts log2(makespan / lower bound) of an order from
  * position-ordered kernel descriptors; it is trained on orders the exact
  * simulator labels, proposes the best-predicted of many random candidates,
- * and every proposal is rescored exactly, so the simulator stays the judge.
+ * and every proposal is rescored exactly, so every reported makespan is the
+ * simulator's.
  *
  * Network: 192 inputs -> 256 -> 256 -> 256 -> 1, ReLU, BF16 weights and
  * activations, FP32 accumulation on tensor cores; MSE loss; Adam

@@ -2,7 +2,7 @@
 // proposal of orders for sets too large to enumerate, every proposal rescored
 // exactly by the run-length simulator.  (The paper has no learned component;
 // this serves the same goal as Algorithm 1 -- a good launch order without
-// trying all N! -- and is judged by the exact simulator.)
+// trying all N! -- and every result it returns is an exactly simulated makespan.)
 #include <algorithm>
 #include <cmath>
 #include <cstring>
