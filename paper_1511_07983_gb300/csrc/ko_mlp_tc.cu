@@ -10,29 +10,34 @@
 //    M = 128, N = 256, K = 16, FP32 accumulator in 256 TMEM columns) and a
 //    tcgen05.commit that arrives on an mbarrier; the CTA waits on it with a
 //    bounded spin (an error flag is set if it gives up).
-//  * Epilogue: warp w reads TMEM lanes 32w..32w+31 (= rows) 32 columns at a
-//    time with tcgen05.ld.32x32b.x32, adds the bias, applies ReLU, rounds to
-//    BF16 and stores.
-// Shared memory (192 KB at K = 256) keeps one CTA per SM, so the 256-column
+//  * Epilogue: eight warps; warp w reads TMEM lanes 32 (w % 4) .. +31 (= rows)
+//    and columns 128 (w / 4) .. +127, 32 columns at a time with
+//    tcgen05.ld.32x32b.x32, adds the bias (staged in shared memory),
+//    applies ReLU, rounds to BF16 and passes the 32 x 64-byte piece through a
+//    per-warp staging area (16-byte slots XOR-rotated by row so that both the
+//    row-wise writes and the segment-wise reads are free of bank conflicts);
+//    each store instruction then writes 8 whole 64-byte row segments.
+//  * Operand fills: thread i copies 16 bytes so that 8 consecutive threads
+//    fill one 128-byte core matrix and a warp fills 512 contiguous bytes of
+//    shared memory (no bank conflicts); its global reads are 64-byte runs of
+//    8 rows.
+// Shared memory (209 KB at K = 256) keeps one CTA per SM, so the 256-column
 // TMEM allocation never waits for another CTA.  The grid is persistent (one
 // CTA per SM): weights are loaded once per CTA, row tiles stream through.
 #include <cstdint>
+#include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "ko_mlp.h"
 
 namespace {
 
 constexpr int kTileM = 128, kTileN = 256;
+constexpr int kThreadsTc = 256;  // 8 warps: warp w drains TMEM lanes 32 (w % 4).. and columns 128 (w / 4)..
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint16_t bf16_bits_tc(float x)
-{
-    uint32_t u = __float_as_uint(x);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
 
 // Shared-memory matrix descriptor (no swizzle): start, leading (K) and stride
 // (8-row) byte offsets in 16-byte units, descriptor version 1 in bits 46-48.
@@ -59,7 +64,7 @@ __device__ __forceinline__ void cp_async16_tc(void *dst, const void *src)
 // to the tensor core's async proxy before each MMA batch; the mbarrier phase
 // alternates per tile.  The next tile's A operand is requested as soon as the
 // current MMAs complete, so its load overlaps the epilogue.
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreadsTc, 1)
 tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt, int K, int tiles,
                 const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
 {
@@ -67,10 +72,20 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, col0 = (warp >> 2) * (kTileN / 2);
     const uint32_t sbo = (uint32_t)(K / 8) * 128u;
     const int kc = K / 8;
     uint8_t *sa = smem;                              // 128 x K
     uint8_t *sb = smem + (size_t)kTileM * K * 2;     // 256 x K
+    float *sbias = (float *)(sb + (size_t)kTileN * K * 2);           // 256
+    uint32_t *stage = (uint32_t *)(sbias + kTileN) + warp * 32 * 16;  // this warp: 32 rows x 16 words
+    // 16-byte chunk i of a rows x K operand: core matrix (r / 8, c), row r % 8
+    auto fill = [&](uint8_t *dst, const uint16_t *src, int rows) {
+        for (int i = tid; i < rows * kc; i += blockDim.x) {
+            const int rlo = i & 7, rest = i >> 3, c = rest % kc, rhi = rest / kc;
+            cp_async16_tc(dst + rhi * sbo + c * 128 + rlo * 16, src + (size_t)(rhi * 8 + rlo) * K + c * 8);
+        }
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(saddr(&tmem_base)));
@@ -80,12 +95,10 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
-    // weights once: 16-byte chunk (row r, k-chunk c) -> (r / 8) * SBO + c * 128 + (r % 8) * 16
-    for (int i = tid; i < kTileN * kc; i += blockDim.x) {
-        const int r = i / kc, c = i % kc;
-        cp_async16_tc(sb + (r >> 3) * sbo + c * 128 + (r & 7) * 16, Wt + (size_t)r * K + c * 8);
-    }
+    // weights and bias once
+    fill(sb, Wt, kTileN);
     asm volatile("cp.async.commit_group;\n" ::);
+    for (int i = tid; i < kTileN; i += blockDim.x) sbias[i] = bias[i];
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
@@ -93,11 +106,7 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
     const uint32_t idesc = instr_desc(kTileM, kTileN);
     // A tile (row tile `tile`) into shared memory with cp.async
     auto load_a = [&](int tile) {
-        const int m0 = tile * kTileM;
-        for (int i = tid; i < kTileM * kc; i += blockDim.x) {
-            const int r = i / kc, c = i % kc;
-            cp_async16_tc(sa + (r >> 3) * sbo + c * 128 + (r & 7) * 16, A + (size_t)(m0 + r) * K + c * 8);
-        }
+        fill(sa, A + (size_t)tile * kTileM * K, kTileM);
         asm volatile("cp.async.commit_group;\n" ::);
     };
     bool ok = true;
@@ -139,10 +148,9 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
             // the MMAs have read the A tile: start loading the next one under the epilogue
             if (tile + (int)gridDim.x < tiles) load_a(tile + gridDim.x);
-            const int row = m0 + warp * 32 + lane;
-            for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            for (int c0 = col0; c0 < col0 + kTileN / 2; c0 += 32) {
                 uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -156,14 +164,26 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
                 uint32_t packed[16];
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.0f);
-                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.0f);
-                    packed[j] = (uint32_t)bf16_bits_tc(x0) | ((uint32_t)bf16_bits_tc(x1) << 16);
+                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.0f);
+                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.0f);
+                    // round to nearest even (cvt.rn.bf16x2): x0 in the low half, x1 in the high half
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                    std::memcpy(&packed[j], &h, sizeof(uint32_t));
                 }
-                uint4 *dst = (uint4 *)(out + (size_t)row * kTileN + c0);
+                // row `lane`'s 64 bytes: 16-byte slot q goes to position (q + lane / 2) % 4
 #pragma unroll
                 for (int q = 0; q < 4; q++)
-                    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                    *(uint4 *)(stage + lane * 16 + ((q + (lane >> 1)) & 3) * 4) =
+                        make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                __syncwarp();
+                // 8 rows per store: lanes 4r..4r+3 write row r's 64 contiguous bytes
+#pragma unroll
+                for (int it = 0; it < 4; it++) {
+                    const int r = it * 8 + (lane >> 2), q = lane & 3;
+                    const uint4 w = *(const uint4 *)(stage + r * 16 + ((q + (r >> 1)) & 3) * 4);
+                    *(uint4 *)(out + (size_t)(m0 + quarter * 32 + r) * kTileN + c0 + q * 8) = w;
+                }
+                __syncwarp();
             }
         }
         // every warp has drained the accumulator before the next tile's MMAs overwrite it
@@ -181,7 +201,8 @@ cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K,
                             int *err, cudaStream_t st)
 {
     if (M % kTileM || (K != 192 && K != 256)) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(kTileM + kTileN) * K * 2;
+    const size_t smem = (size_t)(kTileM + kTileN) * K * 2 + sizeof(float) * kTileN +
+                        (kThreadsTc / 32) * 32 * 16 * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(tc_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -189,7 +210,7 @@ cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = M / kTileM;
     const int grid = tiles < sms ? tiles : sms;
-    tc_layer_kernel<<<grid, 128, smem, st>>>(A, Wt, K, tiles, bias, out, err);
+    tc_layer_kernel<<<grid, kThreadsTc, smem, st>>>(A, Wt, K, tiles, bias, out, err);
     ko_count_launch();
     return cudaGetLastError();
 }
