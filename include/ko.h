@@ -372,14 +372,20 @@ ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_
  * 0 = warp-level mma.sync BF16 GEMMs, 1 = tcgen05 MMAs with TMEM
  * accumulators (default; used for batches that are multiples of 128, the
  * others fall back to mma.sync).  Both give the same bits.  A tcgen05 completion wait that
- * gives up makes the next call return KO_ERR_TIMEOUT.  Training always uses
- * mma.sync.  KO_ERR_ARG for an unknown key or value (below). */
+ * gives up makes the next call return KO_ERR_TIMEOUT.  KO_ERR_ARG for an
+ * unknown key or value (below). */
 #define KO_MODEL_OPT_TC 1
 /* KO_MODEL_OPT_CHUNK: candidate rows per forward pass in ko_surrogate_propose
  * and ko_surrogate_search (a multiple of 1024 in [1024, 2^22], default 262144);
  * larger chunks amortise each layer's weight load over more row tiles and
  * hold chunk x 1 KB of activations.  Results do not depend on it. */
 #define KO_MODEL_OPT_CHUNK 2
+/* KO_MODEL_OPT_TC_TRAIN: training GEMMs (forward with transposed copies,
+ * input and weight gradients) on tcgen05 (1, default; batches that are
+ * multiples of 128, weight gradients of multiples of 256, split-K with a
+ * fixed-order reduction) or on warp-level mma.sync (0).  The two paths
+ * accumulate in different orders, so their gradients agree to rounding. */
+#define KO_MODEL_OPT_TC_TRAIN 3
 ko_status ko_model_set_option(ko_model *m, int32_t key, int64_t value);
 
 void ko_model_destroy(ko_model *m);

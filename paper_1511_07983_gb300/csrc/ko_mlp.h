@@ -35,6 +35,20 @@ cudaError_t ko_mlp_gemm_relu(const uint16_t *A, int lda, const uint16_t *Bt, int
 // K in {192, 256}, N = 256; *err set to 1 if the MMA completion wait gave up.
 cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
                             int *err, cudaStream_t st);
+// tcgen05 training forward layer: also writes out_t = out transposed
+// ([256][ldt] BF16, ldt % 8 == 0).  Same shapes as ko_mlp_layer_tc.
+cudaError_t ko_mlp_layer_tc_t(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
+                              uint16_t *out_t, long long ldt, int *err, cudaStream_t st);
+// tcgen05 input gradient: outf[M][256] = A Wt^T in FP32 (M % 128 == 0, K in {192, 256}).
+cudaError_t ko_mlp_layer_tc_f32(const uint16_t *A, const uint16_t *Wt, int M, int K, float *outf, int *err,
+                                cudaStream_t st);
+// tcgen05 weight gradient: out[M][256] (row stride ldo) = A Bt^T with
+// A [M][Kdim] (row stride lda), Bt [256][Kdim] (row stride ldb), M <= 256,
+// Kdim % 256 == 0; split-K over 256-wide slices into `work`
+// (ko_mlp_wgrad_tc_workspace bytes), summed in a fixed order.
+size_t ko_mlp_wgrad_tc_workspace(int M, long long Kdim);
+cudaError_t ko_mlp_wgrad_tc(const uint16_t *A, long long lda, const uint16_t *Bt, long long ldb, int M,
+                            long long Kdim, float *out, int ldo, float *work, int *err, cudaStream_t st);
 cudaError_t ko_mlp_gemm_f32(const uint16_t *A, int lda, const uint16_t *Bt, int ldb, int M, int N, int K,
                             float *out, int ldo, cudaStream_t st);
 cudaError_t ko_mlp_encode(const int8_t *rows, int row_stride, const int *sid, const int *pick,

@@ -79,6 +79,9 @@ struct ko_model {
     int *pick = nullptr;
     KoFastState fast{};
     int tc_forward = 1;        // inference layers on tcgen05 (1) or mma.sync (0)
+    int tc_train = 1;          // training GEMMs on tcgen05 (1) or mma.sync (0)
+    float *wg_work = nullptr;  // split-K partials of the tcgen05 weight gradients
+    size_t wg_bytes = 0;
     int chunk = 262144;        // candidate rows per forward pass of the proposal paths
     int *tc_err = nullptr;     // device flag: a tcgen05 completion wait gave up
 
@@ -94,7 +97,7 @@ struct ko_model {
     ~ko_model()
     {
         free_acts();
-        cudaFree(p); cudaFree(m); cudaFree(v); cudaFree(g); cudaFree(loss); cudaFree(tc_err);
+        cudaFree(p); cudaFree(m); cudaFree(v); cudaFree(g); cudaFree(loss); cudaFree(tc_err); cudaFree(wg_work);
         cudaFree(w1t); cudaFree(w2); cudaFree(w2t); cudaFree(w3); cudaFree(w3t); cudaFree(w4b);
         ko_fast_release(&fast);
     }
@@ -152,6 +155,22 @@ ko_status refresh_bf16(ko_model *md, cudaStream_t st)
 ko_status forward(ko_model *md, int B, bool train, cudaStream_t st)
 {
     ko_status s;
+    if (train && md->tc_train && B % 128 == 0) {
+        // a layer the tcgen05 path cannot take (shared memory) is refused before launch: use mma.sync
+        const cudaError_t e = ko_mlp_layer_tc_t(md->a0, md->w1t, B, kMlpIn, md->p + kOffB1, md->a1, md->a1t, B,
+                                                md->tc_err, st);
+        if (e == cudaSuccess) {
+            if ((s = cuda_ok(ko_mlp_layer_tc_t(md->a1, md->w2t, B, kHidden, md->p + kOffB2, md->a2, md->a2t, B,
+                                               md->tc_err, st))))
+                return s;
+            if ((s = cuda_ok(ko_mlp_layer_tc(md->a2, md->w3t, B, kHidden, md->p + kOffB3, md->a3, md->tc_err, st))))
+                return s;
+            return cuda_ok(ko_mlp_out_fwd(md->a3, md->w4b, md->p + kOffB4, B, md->y, st));
+        }
+        if (e != cudaErrorInvalidValue) return cuda_ok(e);
+        cudaGetLastError();
+        md->tc_train = 0;
+    }
     if (!train && md->tc_forward && B % 128 == 0) {
         if ((s = cuda_ok(ko_mlp_layer_tc(md->a0, md->w1t, B, kMlpIn, md->p + kOffB1, md->a1, md->tc_err, st)))) return s;
         if ((s = cuda_ok(ko_mlp_layer_tc(md->a1, md->w2t, B, kHidden, md->p + kOffB2, md->a2, md->tc_err, st)))) return s;
@@ -172,6 +191,38 @@ ko_status forward(ko_model *md, int B, bool train, cudaStream_t st)
 
 // Gradients of the mean squared error into md->g (zeroed here); loss sum
 // added to *loss_dev.
+// tcgen05 weight and input gradients (B % 256 == 0), the mma.sync ones otherwise.
+ko_status wgrad(ko_model *md, const uint16_t *at, int M, int B, float *out, cudaStream_t st)
+{
+    if (md->tc_train && B % 256 == 0) {
+        const size_t need = ko_mlp_wgrad_tc_workspace(M, B);
+        if (md->wg_bytes < need) {
+            cudaFree(md->wg_work);
+            md->wg_work = nullptr;
+            md->wg_bytes = 0;
+            if (cudaMalloc(&md->wg_work, need) != cudaSuccess) {
+                cudaGetLastError();
+                return KO_ERR_NOMEM;
+            }
+            md->wg_bytes = need;
+        }
+        const cudaError_t e = ko_mlp_wgrad_tc(at, B, md->dzt, B, M, B, out, kHidden, md->wg_work, md->tc_err, st);
+        if (e != cudaErrorInvalidValue) return cuda_ok(e);
+        cudaGetLastError();
+    }
+    return cuda_ok(ko_mlp_gemm_f32(at, B, md->dzt, B, M, kHidden, B, out, kHidden, st));
+}
+
+ko_status dgrad(ko_model *md, const uint16_t *w, int B, cudaStream_t st)
+{
+    if (md->tc_train && B % 128 == 0) {
+        const cudaError_t e = ko_mlp_layer_tc_f32(md->dz, w, B, kHidden, md->da, md->tc_err, st);
+        if (e != cudaErrorInvalidValue) return cuda_ok(e);
+        cudaGetLastError();
+    }
+    return cuda_ok(ko_mlp_gemm_f32(md->dz, kHidden, w, kHidden, B, kHidden, kHidden, md->da, kHidden, st));
+}
+
 ko_status backward(ko_model *md, int B, float *loss_dev, cudaStream_t st)
 {
     ko_status s;
@@ -179,6 +230,15 @@ ko_status backward(ko_model *md, int B, float *loss_dev, cudaStream_t st)
     if ((s = cuda_ok(ko_mlp_out_bwd(md->y, md->t, md->a3, md->w4b, B, loss_dev, md->g + kOffW4, md->g + kOffB4,
                                     md->g + kOffB3, md->dz, md->dzt, st))))
         return s;
+    if (md->tc_train) {
+        if ((s = wgrad(md, md->a2t, kHidden, B, md->g + kOffW3, st))) return s;
+        if ((s = dgrad(md, md->w3, B, st))) return s;
+        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a2, B, md->g + kOffB2, md->dz, md->dzt, st)))) return s;
+        if ((s = wgrad(md, md->a1t, kHidden, B, md->g + kOffW2, st))) return s;
+        if ((s = dgrad(md, md->w2, B, st))) return s;
+        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a1, B, md->g + kOffB1, md->dz, md->dzt, st)))) return s;
+        return wgrad(md, md->a0t, kMlpIn, B, md->g + kOffW1, st);
+    }
     // layer 3
     if ((s = cuda_ok(ko_mlp_gemm_f32(md->a2t, B, md->dzt, B, kHidden, kHidden, B, md->g + kOffW3, kHidden, st))))
         return s;
@@ -285,6 +345,12 @@ ko_status ko_model_option(ko_model *md, int key, long long value)
     if (key == KO_MODEL_OPT_TC) {
         if (value != 0 && value != 1) return KO_ERR_ARG;
         md->tc_forward = (int)value;
+        if (cudaMemset(md->tc_err, 0, sizeof(int)) != cudaSuccess) return KO_ERR_CUDA;
+        return KO_OK;
+    }
+    if (key == KO_MODEL_OPT_TC_TRAIN) {
+        if (value != 0 && value != 1) return KO_ERR_ARG;
+        md->tc_train = (int)value;
         if (cudaMemset(md->tc_err, 0, sizeof(int)) != cudaSuccess) return KO_ERR_CUDA;
         return KO_OK;
     }
@@ -452,6 +518,7 @@ ko_status ko_model_train_sets(ko_model *md, const KoSet *const *hs, int nsets, l
             for (int i = 0; i < steps; i++) loss_curve[i] = lc[i] / (float)batch;
         }
         if (cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;
+        if (!s) s = ko_model_check(md);  // a tcgen05 completion wait that gave up
     } while (false);
     cudaFree(rows); cudaFree(ms); cudaFree(targets); cudaFree(sid); cudaFree(d_chunk);
     return s;

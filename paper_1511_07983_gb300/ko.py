@@ -383,6 +383,10 @@ class Model:
         """Inference layers on tcgen05 (True) or warp-level mma.sync (False)."""
         _check(lib().ko_model_set_option(self.m, 1, int(bool(on))), "ko_model_set_option")
 
+    def set_tc_train(self, on: bool):
+        """Training GEMMs on tcgen05 (True) or warp-level mma.sync (False)."""
+        _check(lib().ko_model_set_option(self.m, 3, int(bool(on))), "ko_model_set_option")
+
     def set_chunk(self, rows: int):
         """Candidate rows per forward pass of propose/search (multiple of 1024)."""
         _check(lib().ko_model_set_option(self.m, 2, int(rows)), "ko_model_set_option")

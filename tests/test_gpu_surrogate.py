@@ -175,3 +175,49 @@ def test_chunk_size_does_not_change_results(ko):
                 m.set_chunk(bad)
     m.close()
     assert out[0] == out[1] == out[2]
+
+
+@pytest.mark.parametrize("B", [256, 1024, 4096])
+def test_tcgen05_training_gradients(ko, B):
+    # weight gradients split over B / 256 K slices (W1's 192 rows padded to 256), input gradients
+    # and the training forward with transposed copies, against the oracle and the mma.sync path
+    p = _params(11)
+    x = _features(12, B)
+    t = np.random.default_rng(13).standard_normal(B).astype(np.float32)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    m.set_tc_train(True)
+    g_tc, loss_tc = m.grad(x, t)
+    g_tc2, _ = m.grad(x, t)
+    m.set_tc_train(False)
+    g_mma, loss_mma = m.grad(x, t)
+    m.close()
+    # the weight gradients' split-K slices are summed in a fixed order: bit-identical runs
+    # (bias gradients are summed with atomics in the shared elementwise kernels)
+    a, b = _split(g_tc), _split(g_tc2)
+    for k in ("W1", "W2", "W3"):
+        assert (a[k] == b[k]).all(), k
+    assert loss_tc == pytest.approx(loss_mma, rel=1e-3)
+    y, cache = mlp.forward(p, x)
+    want = mlp.backward(p, cache, y, t)
+    got, ref = _split(g_tc), _split(g_mma)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
+        nrm = max(np.linalg.norm(want[k]), 1e-12)
+        assert np.linalg.norm(got[k] - want[k]) / nrm <= 2e-2, (k, "oracle")
+        assert np.linalg.norm(got[k] - ref[k]) / max(np.linalg.norm(ref[k]), 1e-12) <= 1e-2, (k, "mma")
+
+
+def test_tcgen05_training_run(ko):
+    sets = [synth.gen_set("train", 2000 + i) for i in range(8)]
+    curves = []
+    for tc in (True, False):
+        gpus = [ko.Gpu.from_set(s) for s in sets]
+        m = ko.Model(seed=3)
+        m.set_tc_train(tc)
+        curves.append(m.train(gpus, pairs_per_set=4096, steps=200, batch=4096, lr=1e-3, seed=5))
+        m.close()
+        for g in gpus:
+            g.close()
+    a, b = (float(np.mean(c[-20:])) for c in curves)
+    assert a < float(np.mean(curves[0][:5]))      # it learns
+    assert a == pytest.approx(b, rel=0.1)         # like the mma.sync path
