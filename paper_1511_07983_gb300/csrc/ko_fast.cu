@@ -54,7 +54,7 @@ __constant__ unsigned long long c_fact[21] = {
 
 struct SetConst {
     int n, S, R, Sh, W, Bk;
-    long long ccap, mcap;
+    uint32_t ccap, mcap;  // <= 2^30 (the capacity setter rejects more)
     int cshift, mshift;
     int total_blocks;
     int r[KO_MAX_KERNELS], s[KO_MAX_KERNELS], w[KO_MAX_KERNELS], b[KO_MAX_KERNELS];
@@ -285,15 +285,14 @@ struct Sim {
 
     __device__ __forceinline__ uint32_t duration(const SetConst &K, int kid) const
     {
-        const unsigned long long c = (unsigned long long)K.c[kid];
-        const unsigned long long m = (unsigned long long)K.m[kid];
-        const unsigned long long sc = (unsigned long long)max((long long)run.sc, K.ccap);
-        const unsigned long long sm = (unsigned long long)max((long long)run.sm, K.mcap);
-        unsigned long long dc, dm;
-        if (K.cshift >= 0) dc = (c * sc + (unsigned long long)K.ccap - 1) >> K.cshift;
-        else dc = (c * sc + (unsigned long long)K.ccap - 1) / (unsigned long long)K.ccap;
-        if (K.mshift >= 0) dm = (m * sm + (unsigned long long)K.mcap - 1) >> K.mshift;
-        else dm = (m * sm + (unsigned long long)K.mcap - 1) / (unsigned long long)K.mcap;
+        // every factor fits 32 bits (c, m <= 2^24; SumC, SumM <= 32 * 2^24; caps <= 2^30), so each
+        // product is one 32 x 32 -> 64-bit multiply
+        const uint32_t c = (uint32_t)K.c[kid], m = (uint32_t)K.m[kid];
+        const uint32_t sc = max((uint32_t)run.sc, K.ccap), sm = max((uint32_t)run.sm, K.mcap);
+        const unsigned long long pc = (unsigned long long)c * sc + (K.ccap - 1u);
+        const unsigned long long pm = (unsigned long long)m * sm + (K.mcap - 1u);
+        const unsigned long long dc = K.cshift >= 0 ? pc >> K.cshift : pc / K.ccap;
+        const unsigned long long dm = K.mshift >= 0 ? pm >> K.mshift : pm / K.mcap;
         return (uint32_t)(dc > dm ? dc : dm);
     }
 
@@ -460,7 +459,7 @@ __device__ void load_set(SetConst &K, const KoSet *d, const Seg<LANES> &sg)
     nb = (int)__reduce_add_sync(sg.mask, (unsigned)nb);
     if (sg.lane == 0) {
         K.n = d->n; K.S = d->S; K.R = d->R; K.Sh = d->Sh; K.W = d->W; K.Bk = d->Bk;
-        K.ccap = d->ccap; K.mcap = d->mcap; K.cshift = d->cshift; K.mshift = d->mshift;
+        K.ccap = (uint32_t)d->ccap; K.mcap = (uint32_t)d->mcap; K.cshift = d->cshift; K.mshift = d->mshift;
         K.total_blocks = nb;
     }
     __syncwarp(sg.mask);
