@@ -70,3 +70,18 @@ def test_traffic_figure_only_for_unchanged_kernel_sources(tmp_path, monkeypatch)
     assert bench.measured_traffic("other") is None
     (csrc / "ko_fast.cu").write_text("kernel B")
     assert bench.measured_traffic("w") is None
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+                                     "--cpu-sample", "2000"])
+    assert bench.main() == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["metric"] == bench.METRIC and line["unit"] == "orders/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
