@@ -64,3 +64,20 @@ def test_device_buffers_and_invalid_rows(ko):
     assert host[1] == -1.0 and host[2] == -1.0
     assert host[0] == oracle.makespans_ps(s.gpu, s.kernels, rows[:1].astype(np.int32))[0]
     assert d_out.cpu().numpy().tolist() == host.tolist()
+
+
+def test_degenerate_sets(ko):
+    # one kernel, one block; a single kernel filling every SM in one wave; 1024 SMs
+    cases = [((4, 65536, 49152, 64, 8, 100, 100), [[1024, 0, 2, 1, 50, 7]]),
+             ((4, 65536, 49152, 64, 4, 1500, 1 << 30), [[1024, 0, 2, 16, 1000, 1]]),
+             ((1024, 65536, 233472, 64, 32, 32768, 32768), [[4096, 8192, 4, 900, 3000, 700],
+                                                            [2048, 0, 2, 3000, 1200, 4000]])]
+    for gpu, kern in cases:
+        g = ko.Gpu(*gpu[:5], c_cap=gpu[5], m_cap=gpu[6])
+        for row in kern:
+            g.add_kernel(*row)
+        rows = np.array([list(p) for p in __import__("itertools").permutations(range(len(kern)))], dtype=np.int8)
+        got = g.eval_orders_ps(rows)
+        want = oracle.makespans_ps(gpu, kern, rows.astype(np.int32))
+        assert got.view(np.uint64).tolist() == want.view(np.uint64).tolist()
+    assert want.min() > 0

@@ -91,3 +91,8 @@ def test_study_ranks_are_consistent(ko):
         # local search from Algorithm 1 never ends above its start
         assert r["ls_swap_from_alg1"]["makespan"] <= r["alg1_per_sm"]["makespan"]
         assert r["ls_swap_move_from_alg1"]["makespan"] <= r["alg1_per_sm"]["makespan"]
+
+
+def test_large_gpu_twenty_four_kernels(ko):
+    s = synth.gen_set("large", 2)          # N = 24 on one of the three GPUs
+    _check(ko, s, None, False, max_iters=3)
