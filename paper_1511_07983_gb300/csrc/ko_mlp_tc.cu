@@ -212,14 +212,14 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
             for (int c0 = col0; c0 < col0 + kTileN / 2; c0 += 32) {
                 uint32_t v[32];
                 tc_ld32(tmem, quarter, c0, v);
-                if (MODE == 2) {
+                if constexpr (MODE == 2) {
                     float4 *dst = (float4 *)(outf + (size_t)(row0 + lane) * kTileN + c0);
 #pragma unroll
                     for (int q = 0; q < 8; q++)
                         dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
                                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
                     continue;
-                }
+                } else {
                 uint32_t packed[16];
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
@@ -270,6 +270,7 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
                     for (int q = 0; q < 4; q++)
                         dt[q] = make_uint4(col[4 * q], col[4 * q + 1], col[4 * q + 2], col[4 * q + 3]);
                     __syncwarp();
+                }
                 }
             }
         }
