@@ -37,7 +37,9 @@
 #include <cstdint>
 #include <cstring>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "ko_mlp.h"
 
@@ -281,6 +283,161 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
 }
 
+// Inference layer (MODE 0 arithmetic) with operands loaded by TMA.  A 2-D box
+// of 8 elements (16 bytes) x R rows lands one K chunk of R rows as R x 16
+// contiguous bytes: a column of R / 8 core matrices, so the operand layout is
+// K-chunk-major (chunk c at c * R * 16 bytes) and the MMA descriptors take
+// LBO = R * 16 bytes (adjacent along K) and SBO = 128 bytes (adjacent 8-row
+// groups).  One thread issues K/8 box copies per operand, counted in bytes on
+// an mbarrier (expect_tx); the weights (R = 256) and the first A tile (R = 128)
+// arrive together, each later A tile as soon as the previous tile's MMAs have
+// retired.  Epilogue as tc_layer_kernel<0>.
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void expect_bytes(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(mbar)), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1)
+tc_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int K, int tiles,
+              const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar_mma, mbar_load;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, col0 = (warp >> 2) * (kTileN / 2);
+    const int kc = K / 8;
+    uint8_t *sa = smem;                              // kc chunks x 128 rows x 16 B
+    uint8_t *sb = smem + (size_t)kTileM * K * 2;     // kc chunks x 256 rows x 16 B
+    float *sbias = (float *)(sb + (size_t)kTileN * K * 2);
+    uint32_t *stage = (uint32_t *)(sbias + kTileN) + warp * 32 * kStageRowWords;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(saddr(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar_mma)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar_load)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < tiles) {
+        expect_bytes(&mbar_load, (uint32_t)((kTileN + kTileM) * K * 2));
+        for (int c = 0; c < kc; c++) {
+            tma_box(saddr(sb) + (uint32_t)(c * kTileN * 16), &tmW, c * 8, 0, &mbar_load);
+            tma_box(saddr(sa) + (uint32_t)(c * kTileM * 16), &tmA, c * 8, blockIdx.x * kTileM, &mbar_load);
+        }
+    }
+    for (int i = tid; i < kTileN; i += blockDim.x) sbias[i] = bias[i];
+    tc_fence_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = instr_desc(kTileM, kTileN);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, phase ^= 1u) {
+        const int m0 = tile * kTileM;
+        if (!tc_wait(&mbar_load, phase, err)) { ok = false; break; }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            for (int k = 0; k < K / 16; k++) {
+                // a 16-wide K step covers chunks 2k and 2k + 1
+                const uint64_t ad = smem_desc(saddr(sa) + (uint32_t)(2 * k * kTileM * 16), kTileM * 16, 128u);
+                const uint64_t bd = smem_desc(saddr(sb) + (uint32_t)(2 * k * kTileN * 16), kTileN * 16, 128u);
+                const uint32_t acc = k > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                saddr(&mbar_mma)));
+        }
+        if (!tc_wait(&mbar_mma, phase, err)) {
+            ok = false;
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            // the MMAs have read the A tile: fetch the next one under the epilogue
+            const int tn = tile + (int)gridDim.x;
+            if (tid == 0 && tn < tiles) {
+                expect_bytes(&mbar_load, (uint32_t)(kTileM * K * 2));
+                for (int c = 0; c < kc; c++)
+                    tma_box(saddr(sa) + (uint32_t)(c * kTileM * 16), &tmA, c * 8, tn * kTileM, &mbar_load);
+            }
+            const int row0 = m0 + quarter * 32;
+            for (int c0 = col0; c0 < col0 + kTileN / 2; c0 += 32) {
+                uint32_t v[32];
+                tc_ld32(tmem, quarter, c0, v);
+                uint32_t packed[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const float x0 = fmaxf(__uint_as_float(v[2 * q]) + sbias[c0 + 2 * q], 0.0f);
+                    const float x1 = fmaxf(__uint_as_float(v[2 * q + 1]) + sbias[c0 + 2 * q + 1], 0.0f);
+                    packed[q] = pack_bf16(x0, x1);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    *(uint4 *)(stage + lane * 16 + ((q + (lane >> 1)) & 3) * 4) =
+                        make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int it = 0; it < 4; it++) {
+                    const int r = it * 8 + (lane >> 2), q = lane & 3;
+                    const uint4 w = *(const uint4 *)(stage + r * 16 + ((q + (r >> 1)) & 3) * 4);
+                    *(uint4 *)(out + (size_t)(row0 + r) * kTileN + c0 + q * 8) = w;
+                }
+                __syncwarp();
+            }
+        }
+        // every warp has drained the accumulator before the next tile's MMAs overwrite it
+        tc_fence_sync();
+    }
+    // a load still in flight (only after a failed wait) must land before the CTA exits
+    if (!ok && tid == 0) tc_wait(&mbar_load, phase, err);
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// rows x K BF16 matrix (row-major, K contiguous), boxes of 8 x box_rows.
+bool encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, int K, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)base & 15u) || (K * 2) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Weight gradient slice: CTA (mt, s) multiplies rows 128 mt.. of A (M x Kdim,
 // row stride lda) by all 256 rows of Bt (256 x Kdim, row stride ldb) over the
 // K slice 256 s .. 256 s + 255 and writes the FP32 128 x 256 partial tile to
@@ -379,7 +536,23 @@ cudaError_t launch_layer(const uint16_t *A, const uint16_t *Wt, int M, int K, co
 cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
                             int *err, cudaStream_t st)
 {
-    return launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
+    if (M % kTileM || (K != 192 && K != 256)) return cudaErrorInvalidValue;
+    CUtensorMap tma, tmw;
+    const size_t smem = (size_t)(kTileM + kTileN) * K * 2 + sizeof(float) * kTileN +
+                        (kThreadsTc / 32) * 32 * kStageRowWords * sizeof(uint32_t);
+    if ((long long)smem > (long long)max_dyn_smem() || !encode_operand(&tma, A, M, K, kTileM) ||
+        !encode_operand(&tmw, Wt, kTileN, K, kTileN))
+        return launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
+    cudaError_t e = cudaFuncSetAttribute(tc_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = M / kTileM;
+    const int grid = tiles < sms ? tiles : sms;
+    tc_tma_kernel<<<grid, kThreadsTc, smem, st>>>(tma, tmw, K, tiles, bias, out, err);
+    ko_count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t ko_mlp_layer_tc_t(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
