@@ -492,10 +492,20 @@ __device__ __forceinline__ int find_chunk(const KoChunk *chunks, int nchunks, lo
 }
 
 // Per-segment running statistics of the set being worked on.
+// Min, max and better / equal / worse counts of a run of makespans.  The
+// kernel keeps one per segment for the current work item and one for the
+// segment's current set in shared memory (only lane 0 touches them), which
+// keeps twenty 32-bit registers out of the simulation loop.
 struct SegStats {
-    int set = -1;
-    unsigned long long mn = ~0ull, mx = 0, nb = 0, ne = 0, nw = 0;
-    __device__ void flush(KoAccum *accs)
+    unsigned long long mn, mx, nb, ne, nw;
+    __device__ void clear() { mn = ~0ull; mx = 0; nb = ne = nw = 0; }
+    __device__ void add(const SegStats &o)
+    {
+        mn = o.mn < mn ? o.mn : mn;
+        mx = o.mx > mx ? o.mx : mx;
+        nb += o.nb; ne += o.ne; nw += o.nw;
+    }
+    __device__ void flush(KoAccum *accs, int set)
     {
         if (set >= 0 && accs) {
             KoAccum *a = accs + set;
@@ -505,7 +515,7 @@ struct SegStats {
             if (ne) atomicAdd(&a->n_equal, ne);
             if (nw) atomicAdd(&a->n_worse, nw);
         }
-        mn = ~0ull; mx = 0; nb = ne = nw = 0;
+        clear();
     }
 };
 
@@ -541,7 +551,10 @@ fast_kernel(KoWork a)
     }
     SetConst &K = Ks[seg];
     int loaded = -1;
-    SegStats st;    // meaningful on lane 0
+    __shared__ SegStats seg_stats[kSegs], item_stats[kSegs];
+    SegStats &st = seg_stats[seg], &is = item_stats[seg];  // lane 0 only
+    int st_set = -1;                                      // set that `st` accumulates (lane 0)
+    if (sim.sg.lane == 0) st.clear();
 
     for (;;) {
         unsigned long long item = 0;
@@ -559,9 +572,9 @@ fast_kernel(KoWork a)
             load_set<LANES>(K, a.sets + ch.set, sim.sg);
             loaded = ch.set;
         }
-        if (sim.sg.lane == 0 && st.set != ch.set) {
-            st.flush(a.accs);
-            st.set = ch.set;
+        if (sim.sg.lane == 0 && st_set != ch.set) {
+            st.flush(a.accs, st_set);
+            st_set = ch.set;
         }
         const int n = K.n;
         const uint32_t all = (1u << n) - 1u;
@@ -604,7 +617,7 @@ fast_kernel(KoWork a)
         // One walk per item: depths below d0 take the prefix kernel, depths from
         // d0 on enumerate the unused kernels in increasing id (lexicographic DFS),
         // restoring the saved node state for every child after the first.
-        unsigned long long imin = ~0ull, imax = 0, ib = 0, ie = 0, iw = 0;
+        if (sim.sg.lane == 0) is.clear();
         long long leaf = 0;
         int next[KO_MAX_KERNELS + 1];
         int depth = 0;
@@ -642,9 +655,9 @@ fast_kernel(KoWork a)
                     // evict-first: the makespan stream must not push the node-state slab out of L2
                     if (a.out) __stcs((long long *)&a.out[outpos + leaf], (long long)ms);
                     const unsigned long long u = (unsigned long long)ms;
-                    imin = u < imin ? u : imin;
-                    imax = u > imax ? u : imax;
-                    ib += ms < ref; ie += ms == ref; iw += ms > ref;
+                    is.mn = u < is.mn ? u : is.mn;
+                    is.mx = u > is.mx ? u : is.mx;
+                    is.nb += ms < ref; is.ne += ms == ref; is.nw += ms > ref;
                 }
                 leaf++;
                 if (d0 == n) break;
@@ -666,12 +679,10 @@ fast_kernel(KoWork a)
                 if (slot < a.ov_cap) a.ov_list[slot] = item;
             }
         } else if (sim.sg.lane == 0) {
-            st.mn = imin < st.mn ? imin : st.mn;
-            st.mx = imax > st.mx ? imax : st.mx;
-            st.nb += ib; st.ne += ie; st.nw += iw;
+            st.add(is);
         }
     }
-    if (sim.sg.lane == 0) st.flush(a.accs);
+    if (sim.sg.lane == 0) st.flush(a.accs, st_set);
 }
 
 // Device buffer layout inside KoFastState::buf.
