@@ -553,6 +553,8 @@ fast_kernel(KoWork a)
     int loaded = -1;
     __shared__ SegStats seg_stats[kSegs], item_stats[kSegs];
     SegStats &st = seg_stats[seg], &is = item_stats[seg];  // lane 0 only
+    // where the current item's makespans go and what they are ranked against (lane 0 only)
+    __shared__ long long item_out[kSegs], item_ref[kSegs];
     int st_set = -1;                                      // set that `st` accumulates (lane 0)
     if (sim.sg.lane == 0) st.clear();
 
@@ -578,7 +580,7 @@ fast_kernel(KoWork a)
         }
         const int n = K.n;
         const uint32_t all = (1u << n) - 1u;
-        const long long ref = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
+        if (sim.sg.lane == 0) item_ref[seg] = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
         const long long local = (long long)item - ch.first;
 
         // perm[0 .. d0) is the item's fixed prefix (the whole order in list modes)
@@ -617,8 +619,10 @@ fast_kernel(KoWork a)
         // One walk per item: depths below d0 take the prefix kernel, depths from
         // d0 on enumerate the unused kernels in increasing id (lexicographic DFS),
         // restoring the saved node state for every child after the first.
-        if (sim.sg.lane == 0) is.clear();
-        long long leaf = 0;
+        if (sim.sg.lane == 0) {
+            is.clear();
+            item_out[seg] = outpos;
+        }
         int next[KO_MAX_KERNELS + 1];
         int depth = 0;
         bool first_child = true;
@@ -653,13 +657,14 @@ fast_kernel(KoWork a)
                 const long long ms = sim.finish(K);
                 if (sim.sg.lane == 0) {
                     // evict-first: the makespan stream must not push the node-state slab out of L2
-                    if (a.out) __stcs((long long *)&a.out[outpos + leaf], (long long)ms);
+                    const long long pos = item_out[seg]++;
+                    if (a.out) __stcs((long long *)&a.out[pos], (long long)ms);
                     const unsigned long long u = (unsigned long long)ms;
+                    const long long ref = item_ref[seg];
                     is.mn = u < is.mn ? u : is.mn;
                     is.mx = u > is.mx ? u : is.mx;
                     is.nb += ms < ref; is.ne += ms == ref; is.nw += ms > ref;
                 }
-                leaf++;
                 if (d0 == n) break;
                 used &= ~(1u << cand);
                 next[depth] = cand + 1;
