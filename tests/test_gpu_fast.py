@@ -2,6 +2,7 @@
 equal the oracle's (and the simple device simulator's) for every tuning knob
 setting, including forced hand-over of work items to the simple simulator."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -10,6 +11,8 @@ import oracle
 from paper_1511_07983_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -84,6 +87,45 @@ def test_single12_index_sample(ko, lanes):
         g.configure(lanes=lanes)
         got = g.eval_orders(idx=ids)
     assert np.array_equal(got, oracle.makespans_idx(s.gpu, s.kernels, idx=ids))
+
+
+def test_single12_full_space_as_benchmarked(ko, tmp_path):
+    """The exhaustive N=12 launch in the configuration the benchmark times (the
+    tuned lanes and depth, all 479,001,600 orders): seeded samples of the stored
+    makespans, work-item boundaries and the first and last orders equal the
+    oracle's one by one; the fused reductions agree with the stored makespans."""
+    import shutil
+
+    import torch
+    s = synth.gen_set("single12")
+    n_all = math.factorial(12)
+    cache = tmp_path / "tune.json"
+    shutil.copy(os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"), cache)
+    with ko.Gpu.from_set(s) as g:
+        choice = g.autotune(str(cache))
+        per_item = math.factorial(choice["levels"] + 1)   # orders below one item's fixed prefix
+        out = torch.empty(n_all, dtype=torch.int64, device="cuda")
+        g.eval_all(out)
+        r, hist = g.rank_order(None, nbins=4096)
+        torch.cuda.synchronize()
+        mh = oracle.makespan(s.gpu, s.kernels, g.heuristic_order().tolist())
+
+    items = synth.random_indices(1213, n_all // per_item, 40).astype(np.int64)
+    ids = np.concatenate([synth.random_indices(1212, n_all, 2000).astype(np.int64),
+                          items * per_item, items * per_item + per_item - 1,
+                          [0, 1, per_item - 1, per_item, n_all - per_item, n_all - 2, n_all - 1]])
+    got = out[torch.from_numpy(ids).cuda()].cpu().numpy()
+    assert np.array_equal(got, oracle.makespans_idx(s.gpu, s.kernels, idx=ids.astype(np.uint64)))
+
+    lb, ub = oracle.bounds(s.gpu, s.kernels)
+    mn, mx = int(out.min()), int(out.max())
+    assert lb <= mn <= mx <= ub
+    assert r["makespan"] == mh and r["n_total"] == n_all
+    assert (r["min"], r["max"]) == (mn, mx)
+    assert (r["n_better"], r["n_equal"], r["n_worse"]) == \
+        (int((out < mh).sum()), int((out == mh).sum()), int((out > mh).sum()))
+    bins = torch.div((out - mn) * 4096, mx - mn + 1, rounding_mode="floor")
+    assert np.array_equal(hist.astype(np.int64), torch.bincount(bins, minlength=4096).cpu().numpy())
 
 
 def test_simple_and_fast_agree_on_sets10(ko):
