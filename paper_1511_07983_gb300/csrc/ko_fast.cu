@@ -6,7 +6,9 @@
 // * Runs.  SMs with identical state (usage, SumC, SumM and resident groups
 //   with identical end times) form a run of consecutive SM indices.  One lane
 //   of a LANES-wide segment (16 or 32 lanes of a warp) holds one run in
-//   registers.  Runs are split only where SMs of a run receive different
+//   registers.  The two 16-lane segments of a warp take consecutive work items
+//   and step through their events together, with whole-warp collectives and
+//   per-segment predicates, so they share instructions where their paths agree.  Runs are split only where SMs of a run receive different
 //   numbers of blocks; the number of runs stays small because the round-robin
 //   dispatch treats consecutive SMs alike.
 // * Bulk round-robin.  Placing the head kernel is a water-fill: each SM of
@@ -74,19 +76,14 @@ __device__ __forceinline__ int quot32(int x, int d, float rcp)
     return q;
 }
 
+constexpr unsigned kAll = 0xffffffffu;
+
 template <int LANES>
 struct Seg {
     unsigned mask;   // lanes of this segment
     int lane;        // lane within segment
+    unsigned half;   // segment within the warp (0 for 32-lane segments)
 };
-
-template <int LANES>
-__device__ __forceinline__ unsigned seg_ballot(const Seg<LANES> &sg, bool pred)
-{
-    unsigned b = __ballot_sync(sg.mask, pred);
-    if (LANES == 32) return b;
-    return (b & sg.mask) >> (__ffs(sg.mask) - 1);
-}
 
 // Per-lane run state, held in registers (all array indices are compile-time).
 template <int G>
@@ -114,6 +111,13 @@ __device__ __forceinline__ void slot_set(uint32_t (&a)[G], int g, uint32_t v)
         if (g == i) a[i] = v;
 }
 
+// The simulation of one order by one segment.  The event step (burst,
+// close_burst, advance, finish, place_kernel) is executed by every lane of the
+// warp together: each function takes `act`, false in a segment with nothing to
+// do, which then changes no state, and every collective is a whole-warp
+// operation from which a 16-lane segment reads its own half.  So the two
+// segments of a warp issue one instruction stream and share every instruction
+// where their paths agree, instead of running one after the other.
 template <int LANES, int G>
 struct Sim {
     static constexpr int kG = G;
@@ -126,19 +130,41 @@ struct Sim {
     int run_limit;
     int fail;
 
-    __device__ __forceinline__ int shfl(int v, int src) const
+    // ---- segment collectives, reached by the whole warp
+    __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(kAll, v, src, LANES); }
+    __device__ __forceinline__ unsigned ballot(bool pred) const
     {
-        return __shfl_sync(sg.mask, v, src, LANES);
+        const unsigned b = __ballot_sync(kAll, pred);
+        return LANES == 32 ? b : (b >> (sg.half * 16u)) & 0xffffu;
     }
-    __device__ __forceinline__ uint32_t shflu(uint32_t v, int src) const
+    __device__ __forceinline__ bool any(bool pred) const { return ballot(pred) != 0u; }
+    __device__ __forceinline__ unsigned sum(unsigned v) const
     {
-        return __shfl_sync(sg.mask, v, src, LANES);
+        if (LANES == 32) return __reduce_add_sync(kAll, v);
+        const unsigned s0 = __reduce_add_sync(kAll, sg.half ? 0u : v);
+        const unsigned s1 = __reduce_add_sync(kAll, sg.half ? v : 0u);
+        return sg.half ? s1 : s0;
+    }
+    __device__ __forceinline__ unsigned umax(unsigned v) const
+    {
+        if (LANES == 32) return __reduce_max_sync(kAll, v);
+        const unsigned s0 = __reduce_max_sync(kAll, sg.half ? 0u : v);
+        const unsigned s1 = __reduce_max_sync(kAll, sg.half ? v : 0u);
+        return sg.half ? s1 : s0;
+    }
+    __device__ __forceinline__ unsigned umin(unsigned v) const
+    {
+        if (LANES == 32) return __reduce_min_sync(kAll, v);
+        const unsigned s0 = __reduce_min_sync(kAll, sg.half ? ~0u : v);
+        const unsigned s1 = __reduce_min_sync(kAll, sg.half ? v : ~0u);
+        return sg.half ? s1 : s0;
     }
 
-    __device__ void init(const SetConst &K)
+    __device__ void init(const SetConst &K) { init_sms(sg.lane == 0 ? K.S : 0); }
+    __device__ void init_sms(int sms)  // empty GPU, lane 0's run holding `sms` SMs
     {
         run.beg = 0;
-        run.cnt = sg.lane == 0 ? K.S : 0;
+        run.cnt = sms;
         run.ur = run.us = run.uw = run.ub = run.sc = run.sm = 0;
 #pragma unroll
         for (int g = 0; g < kG; g++) { run.gk[g] = 0; run.ge[g] = 0; }
@@ -148,29 +174,30 @@ struct Sim {
         fail = 0;
     }
 
-    // Split run j at offset x (0 < x < cnt_j): lane j keeps the first x SMs,
-    // lane j+1 takes the rest; later lanes move up one.  `extra` registers move
-    // with the lanes.
-    __device__ void split(int j, int x, int &extra0, int &extra1)
+    // Split run j at offset x (0 < x < cnt_j) where `act`: lane j keeps the
+    // first x SMs, lane j+1 takes the rest; later lanes move up one.  `extra`
+    // registers move with the lanes.
+    __device__ void split(int j, int x, int &extra0, int &extra1, bool act)
     {
-        if (nruns >= run_limit) { fail = 1; return; }
-        const bool up = sg.lane > j;
-#define KO_SHIFT(v) { auto _u = __shfl_up_sync(sg.mask, v, 1, LANES); if (up) v = _u; }
+        bool ok = act;
+        if (ok && nruns >= run_limit) { fail = 1; ok = false; }
+        const bool up = ok && sg.lane > j;
+#define KO_SHIFT(v) { auto _u = __shfl_up_sync(kAll, v, 1, LANES); if (up) v = _u; }
         KO_SHIFT(run.beg) KO_SHIFT(run.cnt) KO_SHIFT(run.ur) KO_SHIFT(run.us) KO_SHIFT(run.uw)
         KO_SHIFT(run.ub) KO_SHIFT(run.sc) KO_SHIFT(run.sm) KO_SHIFT(extra0) KO_SHIFT(extra1)
 #pragma unroll
         for (int g = 0; g < kG; g++) { KO_SHIFT(run.gk[g]) KO_SHIFT(run.ge[g]) }
 #undef KO_SHIFT
-        if (sg.lane == j) run.cnt = x;
-        if (sg.lane == j + 1) { run.beg += x; run.cnt -= x; }
-        nruns++;
+        if (ok && sg.lane == j) run.cnt = x;
+        if (ok && sg.lane == j + 1) { run.beg += x; run.cnt -= x; }
+        if (ok) nruns++;
     }
 
     // Add `give` blocks per SM of kernel kid to this lane's run as a new
-    // pending group.
-    __device__ void add_blocks(const SetConst &K, int kid, int give)
+    // pending group (where `act`).
+    __device__ void add_blocks(const SetConst &K, int kid, int give, bool act)
     {
-        bool need = give > 0 && run.cnt > 0;
+        bool need = act && give > 0 && run.cnt > 0;
         if (need) {
             run.ur += give * K.r[kid];
             run.us += give * K.s[kid];
@@ -187,100 +214,113 @@ struct Sim {
                 placed = true;
             }
         }
-        if (__any_sync(sg.mask, !placed)) fail = 1;
+        if (any(!placed)) fail = 1;
     }
 
     // One dispatch burst for the head kernel `kid` with `left` blocks queued.
-    __device__ void burst(const SetConst &K, int kid, int &left)
+    __device__ void burst(const SetConst &K, int kid, int &left, bool act)
     {
-        const int r = K.r[kid], s = K.s[kid], w = K.w[kid];
+        const int k = act ? kid : 0;  // kernel 0's constants stand in where the segment is idle
+        const int r = K.r[k], s = K.s[k], w = K.w[k];
         int cap = 0;
-        if (run.cnt > 0) {
+        if (act && run.cnt > 0) {
             cap = K.Bk - run.ub;
-            cap = min(cap, quot32(K.R - run.ur, r, K.rr[kid]));
-            cap = min(cap, quot32(K.W - run.uw, w, K.rw[kid]));
-            if (s > 0) cap = min(cap, quot32(K.Sh - run.us, s, K.rs[kid]));
+            cap = min(cap, quot32(K.R - run.ur, r, K.rr[k]));
+            cap = min(cap, quot32(K.W - run.uw, w, K.rw[k]));
+            if (s > 0) cap = min(cap, quot32(K.Sh - run.us, s, K.rs[k]));
             cap = max(cap, 0);
         }
-        const int total = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * cap));
-        if (total == 0) return;
-        const int maxcap = (int)__reduce_max_sync(sg.mask, (unsigned)cap);
-        if (total <= left) {
+        const int total = (int)sum((unsigned)(run.cnt * cap));
+        const int maxcap = (int)umax((unsigned)cap);
+        const bool full = act && total > 0 && total <= left;
+        bool part = act && total > left;
+        int give = 0;
+        {
             // every SM takes its full capacity; the last block lands on the SM
             // with cap == maxcap that comes last cyclically from p
-            int pos = -1;
-            if (run.cnt > 0 && cap == maxcap) {
+            int pos = 0;
+            if (full && run.cnt > 0 && cap == maxcap) {
                 const int pm1 = p == 0 ? K.S - 1 : p - 1;
-                if (pm1 >= run.beg && pm1 < run.beg + run.cnt) pos = K.S - 1;
-                else { pos = run.beg + run.cnt - 1 - p; if (pos < 0) pos += K.S; }
+                if (pm1 >= run.beg && pm1 < run.beg + run.cnt) pos = K.S;
+                else { pos = run.beg + run.cnt - p; if (pos <= 0) pos += K.S; }
             }
-            const int maxpos = __reduce_max_sync(sg.mask, pos);
-            p += maxpos + 1;
-            if (p >= K.S) p -= K.S;
-            left -= total;
-            add_blocks(K, kid, cap);
-            return;
+            const int maxpos = (int)umax((unsigned)pos);  // last SM's cyclic offset from p, plus one
+            if (full) {
+                p += maxpos;
+                if (p >= K.S) p -= K.S;
+                left -= total;
+                give = cap;
+            }
         }
-        // partial placement: smallest sweep count L with F(L) >= left
-        int lo = 1, hi = maxcap;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const int f = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * min(cap, mid)));
-            if (f >= left) hi = mid; else lo = mid + 1;
-        }
-        const int L = lo;
-        const int full = (int)__reduce_add_sync(sg.mask, (unsigned)(run.cnt * min(cap, L - 1)));
-        const int rem = left - full;  // 1 .. number of SMs with cap >= L
-        // Two cuts, one split site: phase 0 cuts the run holding p at p when its
-        // SMs are eligible (so the cyclic order from p is a rotation of whole
-        // runs); phase 1 cuts the run where the last partial sweep ends.
-        int jp = __ffs(seg_ballot(sg, run.cnt > 0 && run.beg <= p && p < run.beg + run.cnt)) - 1;
-        int plus = 0, star = 0, x = 0, beg_star = 0;
-#pragma unroll 1
-        for (int phase = 0; phase < 2; phase++) {
-            int cut_lane, cut_at;
-            bool need;
-            if (phase == 0) {
-                const int beg_jp = shfl(run.beg, jp), cap_jp = shfl(cap, jp);
-                need = beg_jp < p && cap_jp >= L;
-                cut_lane = jp;
-                cut_at = p - beg_jp;
-            } else {
-                const int e = (run.cnt > 0 && cap >= L) ? run.cnt : 0;
-                int incl = e;
-#pragma unroll
-                for (int o = 1; o < LANES; o <<= 1) {
-                    const int v = __shfl_up_sync(sg.mask, incl, o, LANES);
-                    if (sg.lane >= o) incl += v;
+        if (__any_sync(kAll, part)) {
+            // partial placement: smallest sweep count L with F(L) >= left
+            int lo = 1, hi = part ? maxcap : 1;
+            while (__any_sync(kAll, lo < hi)) {
+                const int mid = (lo + hi) >> 1;
+                const int f = (int)sum((unsigned)(run.cnt * min(cap, mid)));
+                if (lo < hi) {
+                    if (f >= left) hi = mid; else lo = mid + 1;
                 }
-                const int excl = incl - e;
-                const int E = shfl(incl, LANES - 1);
-                const int excl_jp = shfl(excl, jp);
-                const int rot = sg.lane >= jp ? excl - excl_jp : E - excl_jp + excl;
-                star = __ffs(seg_ballot(sg, e > 0 && rot < rem && rem <= rot + e)) - 1;
-                x = rem - shfl(rot, star);
-                const int cnt_star = shfl(run.cnt, star);
-                beg_star = shfl(run.beg, star);
-                // rotated position of each lane relative to jp
-                const int rl = sg.lane >= jp ? sg.lane - jp : sg.lane - jp + nruns;
-                const int rs = star >= jp ? star - jp : star - jp + nruns;
-                plus = (e > 0 && rl < rs) ? 1 : 0;
-                if (sg.lane == star) plus = 1;
-                need = x < cnt_star;
-                cut_lane = star;
-                cut_at = x;
             }
-            if (need) {
-                split(cut_lane, cut_at, cap, plus);
-                if (fail) return;
-                if (phase == 0) jp++;
-                else if (sg.lane == star + 1) plus = 0;
+            const int L = lo;
+            const int filled = (int)sum((unsigned)(run.cnt * min(cap, L - 1)));
+            const int rem = left - filled;  // 1 .. number of SMs with cap >= L
+            // Two cuts, one split site: phase 0 cuts the run holding p at p when its
+            // SMs are eligible (so the cyclic order from p is a rotation of whole
+            // runs); phase 1 cuts the run where the last partial sweep ends.
+            int jp = __ffs(ballot(run.cnt > 0 && run.beg <= p && p < run.beg + run.cnt)) - 1;
+            int plus = 0, star = 0, x = 0, beg_star = 0;
+#pragma unroll 1
+            for (int phase = 0; phase < 2; phase++) {
+                int cut_lane, cut_at;
+                bool need;
+                if (phase == 0) {
+                    const int beg_jp = shfl(run.beg, jp), cap_jp = shfl(cap, jp);
+                    need = part && beg_jp < p && cap_jp >= L;
+                    cut_lane = jp;
+                    cut_at = p - beg_jp;
+                } else {
+                    const int e = (run.cnt > 0 && cap >= L) ? run.cnt : 0;
+                    int incl = e;
+#pragma unroll
+                    for (int o = 1; o < LANES; o <<= 1) {
+                        const int v = __shfl_up_sync(kAll, incl, o, LANES);
+                        if (sg.lane >= o) incl += v;
+                    }
+                    const int excl = incl - e;
+                    const int E = shfl(incl, LANES - 1);
+                    const int excl_jp = shfl(excl, jp);
+                    const int rot = sg.lane >= jp ? excl - excl_jp : E - excl_jp + excl;
+                    star = __ffs(ballot(e > 0 && rot < rem && rem <= rot + e)) - 1;
+                    x = rem - shfl(rot, star);
+                    const int cnt_star = shfl(run.cnt, star);
+                    beg_star = shfl(run.beg, star);
+                    // rotated position of each lane relative to jp
+                    const int rl = sg.lane >= jp ? sg.lane - jp : sg.lane - jp + nruns;
+                    const int rs = star >= jp ? star - jp : star - jp + nruns;
+                    plus = (e > 0 && rl < rs) ? 1 : 0;
+                    if (sg.lane == star) plus = 1;
+                    need = part && x < cnt_star;
+                    cut_lane = star;
+                    cut_at = x;
+                }
+                if (__any_sync(kAll, need)) {
+                    split(cut_lane, cut_at, cap, plus, need);
+                    if (need) {
+                        if (fail) part = false;
+                        else if (phase == 0) jp++;
+                        else if (sg.lane == star + 1) plus = 0;
+                    }
+                }
+            }
+            if (part) {
+                p = beg_star + x;
+                if (p >= K.S) p -= K.S;
+                left = 0;
+                give = min(cap, L - 1) + plus;
             }
         }
-        p = beg_star + x;
-        if (p >= K.S) p -= K.S;
-        left = 0;
-        add_blocks(K, kid, min(cap, L - 1) + plus);
+        add_blocks(K, k, give, full || part);
     }
 
     __device__ __forceinline__ uint32_t duration(const SetConst &K, int kid) const
@@ -298,13 +338,15 @@ struct Sim {
 
     // Fix the durations of the groups started in the open burst (one body,
     // looped over the set bits of each lane's pending mask).
-    __device__ void close_burst(const SetConst &K)
+    __device__ void close_burst(const SetConst &K, bool act)
     {
         const uint32_t t32 = (uint32_t)t;
         uint32_t pend = 0;
+        if (act) {
 #pragma unroll
-        for (int g = 0; g < kG; g++) pend |= ((run.gk[g] & kPend) ? 1u : 0u) << g;
-        while (__any_sync(sg.mask, pend != 0)) {
+            for (int g = 0; g < kG; g++) pend |= ((run.gk[g] & kPend) ? 1u : 0u) << g;
+        }
+        while (__any_sync(kAll, pend != 0)) {
             if (pend) {
                 const int g = __ffs(pend) - 1;
                 pend &= pend - 1;
@@ -316,21 +358,26 @@ struct Sim {
     }
 
     // Jump to the earliest end and release every group ending then.
-    __device__ void advance(const SetConst &K)
+    __device__ void advance(const SetConst &K, bool act)
     {
         const uint32_t t32 = (uint32_t)t;
         uint32_t dmin = 0xffffffffu;
+        if (act) {
 #pragma unroll
-        for (int g = 0; g < kG; g++)
-            if (run.gk[g]) dmin = min(dmin, run.ge[g] - t32);
-        dmin = __reduce_min_sync(sg.mask, dmin);
-        if (dmin == 0xffffffffu) { fail = 1; return; }
-        t += dmin;
-        const uint32_t now = t32 + dmin;
+            for (int g = 0; g < kG; g++)
+                if (run.gk[g]) dmin = min(dmin, run.ge[g] - t32);
+        }
+        dmin = umin(dmin);
+        bool ok = act;
+        if (ok && dmin == 0xffffffffu) { fail = 1; ok = false; }
         uint32_t rel = 0;
+        if (ok) {
+            t += dmin;
+            const uint32_t now = t32 + dmin;
 #pragma unroll
-        for (int g = 0; g < kG; g++) rel |= (run.gk[g] != 0 && run.ge[g] == now ? 1u : 0u) << g;
-        while (__any_sync(sg.mask, rel != 0)) {
+            for (int g = 0; g < kG; g++) rel |= (run.gk[g] != 0 && run.ge[g] == now ? 1u : 0u) << g;
+        }
+        while (__any_sync(kAll, rel != 0)) {
             if (rel) {
                 const int g = __ffs(rel) - 1;
                 rel &= rel - 1;
@@ -346,28 +393,34 @@ struct Sim {
 
     // Queue all blocks of kernel kid behind the current queue and simulate
     // until the last of them is placed (the burst that places it stays open).
-    __device__ void place_kernel(const SetConst &K, int kid)
+    // The whole warp runs the loop until no segment has events left.
+    __device__ void place_kernel(const SetConst &K, int kid, bool act)
     {
-        int left = K.b[kid];
-        for (int it = 0; !fail; it++) {
-            burst(K, kid, left);
-            if (left == 0 || fail) break;
-            close_burst(K);
-            advance(K);
-            if (it > K.total_blocks + 64) { fail = 1; break; }  // each event frees >= 1 block
+        int left = act ? K.b[kid] : 0;
+        bool go = act && !fail;
+        int it = 0;
+        while (__any_sync(kAll, go)) {
+            burst(K, kid, left, go);
+            const bool more = go && !fail && left > 0;
+            close_burst(K, more);
+            advance(K, more);
+            if (more && ++it > K.total_blocks + 64) fail = 1;  // each event frees >= 1 block
+            go = more && !fail;
         }
     }
 
-    // Close the final burst; the makespan is the latest end.
-    __device__ long long finish(const SetConst &K)
+    // Close the final burst; the makespan is the latest end (where `act`).
+    __device__ long long finish(const SetConst &K, bool act)
     {
-        close_burst(K);
+        close_burst(K, act);
         const uint32_t t32 = (uint32_t)t;
         uint32_t dmax = 0;
+        if (act) {
 #pragma unroll
-        for (int g = 0; g < kG; g++)
-            if (run.gk[g]) dmax = max(dmax, run.ge[g] - t32);
-        dmax = __reduce_max_sync(sg.mask, dmax);
+            for (int g = 0; g < kG; g++)
+                if (run.gk[g]) dmax = max(dmax, run.ge[g] - t32);
+        }
+        dmax = umax(dmax);
         return t + (long long)dmax;
     }
 
@@ -539,14 +592,18 @@ fast_kernel(KoWork a)
     const int seg = threadIdx.x / LANES;
     sim.sg.lane = threadIdx.x % LANES;
     sim.run_limit = a.run_limit < LANES ? a.run_limit : LANES;
-    sim.sg.mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+    sim.sg.mask = LANES == 32 ? kAll : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
     const int level_words = kStateWords * SAVE + 4;
+    const unsigned half = (threadIdx.x & 31) / LANES;  // segment within the warp
+    sim.sg.half = half;
     // node states: per segment, in shared memory or in a global slab
     int *stack = stack_mem + seg * a.levels * level_words;
     if (a.gstack) {
         const long long gseg = (long long)blockIdx.x * kSegs + seg;
         const long long off = gseg * a.levels * level_words;
-        if (off + (long long)a.levels * level_words > a.gstack_words) return;  // slab too small: never taken
+        // slab too small (never taken): checked for the warp's last segment, so a warp leaves whole
+        const long long last = (long long)blockIdx.x * kSegs + seg + (32 / LANES - 1 - (int)half);
+        if ((last + 1) * a.levels * level_words > a.gstack_words) return;
         stack = a.gstack + off;
     }
     SetConst &K = Ks[seg];
@@ -557,134 +614,161 @@ fast_kernel(KoWork a)
     __shared__ long long item_out[kSegs], item_ref[kSegs];
     int st_set = -1;                                      // set that `st` accumulates (lane 0)
     if (sim.sg.lane == 0) st.clear();
+    sim.init_sms(0);  // a segment without an item still takes part in the warp's event steps
 
+    // The warp's segments take consecutive items together and walk them in step: every
+    // whole-warp operation below (the fetch's shuffles, the walk's vote, the event vote in
+    // place_kernel) is reached by all segments of the warp equally often, and the only exit
+    // from this loop is the same for the whole warp.
+    constexpr int kPerWarp = 32 / LANES;
     for (;;) {
-        unsigned long long item = 0;
-        if (sim.sg.lane == 0) {
-            item = atomicAdd(a.counter, 1ull);
-            if (a.item_list) {  // pass over items a previous pass abandoned
-                const unsigned long long cnt = *a.item_count < a.ov_cap ? *a.item_count : a.ov_cap;
-                item = item < cnt ? a.item_list[item] : ~0ull;
-            }
+        unsigned long long base = 0, lim = 0;
+        if ((threadIdx.x & 31) == 0) {
+            base = atomicAdd(a.counter, (unsigned long long)kPerWarp);
+            lim = (unsigned long long)a.n_items;
+            if (a.item_list)  // pass over items a previous pass abandoned
+                lim = *a.item_count < a.ov_cap ? *a.item_count : a.ov_cap;
         }
-        item = __shfl_sync(sim.sg.mask, item, 0, LANES);
-        if (item >= (unsigned long long)a.n_items) break;
-        const KoChunk ch = a.chunks[find_chunk(a.chunks, a.nchunks, (long long)item)];
-        if (ch.set != loaded) {
-            load_set<LANES>(K, a.sets + ch.set, sim.sg);
-            loaded = ch.set;
-        }
-        if (sim.sg.lane == 0 && st_set != ch.set) {
-            st.flush(a.accs, st_set);
-            st_set = ch.set;
-        }
-        const int n = K.n;
-        const uint32_t all = (1u << n) - 1u;
-        if (sim.sg.lane == 0) item_ref[seg] = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
-        const long long local = (long long)item - ch.first;
+        base = __shfl_sync(kAll, base, 0);
+        lim = __shfl_sync(kAll, lim, 0);
+        if (base >= lim) break;
+        unsigned long long item = base + half;
+        bool have = item < lim;  // an odd tail leaves the last segment without an item
+        if (have && a.item_list) item = a.item_list[item];
+        have = have && item < (unsigned long long)a.n_items;
 
         // perm[0 .. d0) is the item's fixed prefix (the whole order in list modes)
         int8_t perm[KO_MAX_KERNELS];
-        int d0;
-        long long outpos;
-        bool valid = true;
-        uint32_t used = 0;
-        if (ch.mode == 1) {
-            d0 = n;
-            outpos = ch.out_off + local;
-            const unsigned long long k = a.idx[ch.list_off + local];
-            valid = k < c_fact[n];
-            if (valid) lehmer_prefix(n, k, n, perm, used);
-        } else if (ch.mode == 2) {
-            d0 = n;
-            outpos = ch.out_off + local;
-            const int8_t *row = a.perms + ch.list_off + local * (a.perm_stride ? a.perm_stride : n);
-            for (int j = 0; j < n; j++) {
-                const int v = row[j];
-                if (v < 0 || v >= n || ((used >> v) & 1u)) { valid = false; break; }
-                perm[j] = (int8_t)v;
-                used |= 1u << v;
+        int next[KO_MAX_KERNELS + 1];
+        int n = 0, d0 = 0, depth = 0;
+        uint32_t all = 0, used = 0;
+        bool first_child = true;
+        if (have) {
+            const KoChunk ch = a.chunks[find_chunk(a.chunks, a.nchunks, (long long)item)];
+            if (ch.set != loaded) {
+                load_set<LANES>(K, a.sets + ch.set, sim.sg);
+                loaded = ch.set;
             }
-        } else {
-            d0 = ch.d0;
-            const unsigned long long base = (unsigned long long)(ch.list_off + local) * c_fact[n - d0];
-            outpos = ch.out_off + (long long)base;
-            lehmer_prefix(n, base, d0, perm, used);
-        }
-        if (!valid) {
-            if (sim.sg.lane == 0 && a.out) a.out[outpos] = -1;
-            continue;
+            if (sim.sg.lane == 0 && st_set != ch.set) {
+                st.flush(a.accs, st_set);
+                st_set = ch.set;
+            }
+            n = K.n;
+            all = (1u << n) - 1u;
+            if (sim.sg.lane == 0) item_ref[seg] = a.refs ? a.refs[ch.set] : a.sets[ch.set].ref_makespan;
+            const long long local = (long long)item - ch.first;
+            long long outpos;
+            bool valid = true;
+            if (ch.mode == 1) {
+                d0 = n;
+                outpos = ch.out_off + local;
+                const unsigned long long k = a.idx[ch.list_off + local];
+                valid = k < c_fact[n];
+                if (valid) lehmer_prefix(n, k, n, perm, used);
+            } else if (ch.mode == 2) {
+                d0 = n;
+                outpos = ch.out_off + local;
+                const int8_t *row = a.perms + ch.list_off + local * (a.perm_stride ? a.perm_stride : n);
+                for (int j = 0; j < n; j++) {
+                    const int v = row[j];
+                    if (v < 0 || v >= n || ((used >> v) & 1u)) { valid = false; break; }
+                    perm[j] = (int8_t)v;
+                    used |= 1u << v;
+                }
+            } else {
+                d0 = ch.d0;
+                const unsigned long long first = (unsigned long long)(ch.list_off + local) * c_fact[n - d0];
+                outpos = ch.out_off + (long long)first;
+                lehmer_prefix(n, first, d0, perm, used);
+            }
+            if (!valid) {
+                if (sim.sg.lane == 0 && a.out) a.out[outpos] = -1;
+                have = false;
+            } else {
+                if (sim.sg.lane == 0) {
+                    is.clear();
+                    item_out[seg] = outpos;
+                }
+                used = 0;
+                sim.init(K);
+                if (d0 == 0) {
+                    next[0] = 0;
+                    if (n >= 2) sim.template save<SAVE>(stack);
+                }
+            }
         }
 
         // One walk per item: depths below d0 take the prefix kernel, depths from
         // d0 on enumerate the unused kernels in increasing id (lexicographic DFS),
-        // restoring the saved node state for every child after the first.
-        if (sim.sg.lane == 0) {
-            is.clear();
-            item_out[seg] = outpos;
-        }
-        int next[KO_MAX_KERNELS + 1];
-        int depth = 0;
-        bool first_child = true;
-        used = 0;
-        sim.init(K);
-        if (d0 == 0) {
-            next[0] = 0;
-            if (n >= 2) sim.template save<SAVE>(stack);
-        }
-        while (!sim.fail) {
-            int cand;
-            if (depth < d0) {
-                cand = perm[depth];
-            } else {
-                const uint32_t avail = ~used & all & ~((1u << next[depth]) - 1u);
-                if (avail == 0) {
-                    if (depth == d0) break;
+        // restoring the saved node state for every child after the first.  Each
+        // step places one kernel; a segment whose walk has ended still votes.
+        bool going = have && !sim.fail;
+        while (__any_sync(kAll, going)) {
+            int cand = -1;
+            if (going) {
+                for (;;) {  // next kernel to place, backing up as needed (depth falls each turn)
+                    if (depth < d0) { cand = perm[depth]; break; }
+                    const uint32_t avail = ~used & all & ~((1u << next[depth]) - 1u);
+                    if (avail) {
+                        cand = __ffs(avail) - 1;
+                        if (!first_child) sim.template restore<SAVE>(stack + (depth - d0) * level_words);
+                        break;
+                    }
+                    if (depth == d0) break;  // the walk is complete
                     depth--;
                     used &= ~(1u << perm[depth]);
                     next[depth] = perm[depth] + 1;
                     first_child = false;
-                    continue;
                 }
-                cand = __ffs(avail) - 1;
-                if (!first_child) sim.template restore<SAVE>(stack + (depth - d0) * level_words);
-            }
-            perm[depth] = (int8_t)cand;
-            used |= 1u << cand;
-            sim.place_kernel(K, cand);
-            if (sim.fail) break;
-            if (depth + 1 == n) {
-                const long long ms = sim.finish(K);
-                if (sim.sg.lane == 0) {
-                    // evict-first: the makespan stream must not push the node-state slab out of L2
-                    const long long pos = item_out[seg]++;
-                    if (a.out) __stcs((long long *)&a.out[pos], (long long)ms);
-                    const unsigned long long u = (unsigned long long)ms;
-                    const long long ref = item_ref[seg];
-                    is.mn = u < is.mn ? u : is.mn;
-                    is.mx = u > is.mx ? u : is.mx;
-                    is.nb += ms < ref; is.ne += ms == ref; is.nw += ms > ref;
+                if (cand < 0) {
+                    going = false;
+                } else {
+                    perm[depth] = (int8_t)cand;
+                    used |= 1u << cand;
                 }
-                if (d0 == n) break;
-                used &= ~(1u << cand);
-                next[depth] = cand + 1;
-                first_child = false;
-                continue;
             }
-            depth++;
-            if (depth >= d0) {
-                next[depth] = 0;
-                first_child = true;
-                if (n - depth >= 2) sim.template save<SAVE>(stack + (depth - d0) * level_words);
+            sim.place_kernel(K, cand, going);
+            if (going && sim.fail) going = false;
+            const bool leaf = going && depth + 1 == n;
+            long long ms = 0;
+            if (__any_sync(kAll, leaf)) ms = sim.finish(K, leaf);
+            if (going) {
+                if (leaf) {
+                    if (sim.sg.lane == 0) {
+                        // evict-first: the makespan stream must not push the node-state slab out of L2
+                        const long long pos = item_out[seg]++;
+                        if (a.out) __stcs((long long *)&a.out[pos], (long long)ms);
+                        const unsigned long long u = (unsigned long long)ms;
+                        const long long ref = item_ref[seg];
+                        is.mn = u < is.mn ? u : is.mn;
+                        is.mx = u > is.mx ? u : is.mx;
+                        is.nb += ms < ref; is.ne += ms == ref; is.nw += ms > ref;
+                    }
+                    if (d0 == n) {
+                        going = false;
+                    } else {
+                        used &= ~(1u << cand);
+                        next[depth] = cand + 1;
+                        first_child = false;
+                    }
+                } else {
+                    depth++;
+                    if (depth >= d0) {
+                        next[depth] = 0;
+                        first_child = true;
+                        if (n - depth >= 2) sim.template save<SAVE>(stack + (depth - d0) * level_words);
+                    }
+                    if (sim.fail) going = false;
+                }
             }
         }
-        if (sim.fail) {
-            if (sim.sg.lane == 0) {
+        if (have && sim.sg.lane == 0) {
+            if (sim.fail) {
                 const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
                 if (slot < a.ov_cap) a.ov_list[slot] = item;
+            } else {
+                st.add(is);
             }
-        } else if (sim.sg.lane == 0) {
-            st.add(is);
         }
     }
     if (sim.sg.lane == 0) st.flush(a.accs, st_set);
