@@ -534,6 +534,30 @@ __device__ void lehmer_prefix(int n, unsigned long long k, int depth, int8_t *pe
     }
 }
 
+// Order in which a warp's two segments take the prefixes of one exhaustive chunk.  Prefixes
+// of length d0 in lexicographic order fall into groups of m (m - 1) (m = N - d0 + 2) that share
+// all but their last two kernels; inside a group whose items all lie in [lo, hi), item j and
+// j ^ 1 are mapped to two prefixes that end in the same two kernels in swapped order, so the
+// two segments then walk the same remaining kernels in the same order.  A bijection on
+// [lo, hi); items of a group cut by the range keep their place.
+__device__ __forceinline__ unsigned long long pair_swap_order(unsigned long long j, int m, unsigned long long lo,
+                                                              unsigned long long hi)
+{
+    const unsigned long long M = (unsigned long long)m * (m - 1);
+    const unsigned long long g0 = j - j % M;
+    if (g0 < lo || g0 + M > hi) return j;
+    const unsigned v = (unsigned)(j - g0);
+    unsigned q = v >> 1;  // unordered pair {x < y} of the group's last two kernels (ranks)
+    int x = 0;
+    while (q >= (unsigned)(m - 1 - x)) {  // at most m - 1 turns
+        q -= (unsigned)(m - 1 - x);
+        x++;
+    }
+    const int y = x + 1 + (int)q;
+    const int a0 = (v & 1u) ? y : x, a1 = (v & 1u) ? x : y;
+    return g0 + (unsigned long long)a0 * (m - 1) + (unsigned long long)(a1 > a0 ? a1 - 1 : a1);
+}
+
 __device__ __forceinline__ int find_chunk(const KoChunk *chunks, int nchunks, long long item)
 {
     int lo = 0, hi = nchunks - 1;
@@ -636,6 +660,9 @@ fast_kernel(KoWork a)
         bool have = item < lim;  // an odd tail leaves the last segment without an item
         if (have && a.item_list) item = a.item_list[item];
         have = have && item < (unsigned long long)a.n_items;
+        // the index an abandoned item is recorded under: the later passes take items in plain
+        // order, so a reordered prefix is recorded as the item that plain order maps to it
+        unsigned long long rec = item;
 
         // perm[0 .. d0) is the item's fixed prefix (the whole order in list modes)
         int8_t perm[KO_MAX_KERNELS];
@@ -677,7 +704,13 @@ fast_kernel(KoWork a)
                 }
             } else {
                 d0 = ch.d0;
-                const unsigned long long first = (unsigned long long)(ch.list_off + local) * c_fact[n - d0];
+                unsigned long long j = (unsigned long long)(ch.list_off + local);
+                if (kPerWarp == 2 && d0 >= 2) {
+                    j = pair_swap_order(j, n - d0 + 2, (unsigned long long)ch.list_off,
+                                        (unsigned long long)(ch.list_off + ch.count));
+                    rec = (unsigned long long)ch.first + (j - (unsigned long long)ch.list_off);
+                }
+                const unsigned long long first = j * c_fact[n - d0];
                 outpos = ch.out_off + (long long)first;
                 lehmer_prefix(n, first, d0, perm, used);
             }
@@ -765,7 +798,7 @@ fast_kernel(KoWork a)
         if (have && sim.sg.lane == 0) {
             if (sim.fail) {
                 const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
-                if (slot < a.ov_cap) a.ov_list[slot] = item;
+                if (slot < a.ov_cap) a.ov_list[slot] = rec;
             } else {
                 st.add(is);
             }
