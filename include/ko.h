@@ -225,9 +225,12 @@ int64_t ko_get_option(const ko_gpu *g, int32_t key);
 ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream);
 
 /* Work items the last exhaustive or index-list call moved from the
- * run-length simulator to the simple one (a simulation needed more runs of
- * distinct SM states than lanes, or more than 8 resident groups in a run);
- * -1 for a NULL handle.  Informational: results are exact either way. */
+ * run-length simulator to its wider second pass (a simulation needed more runs
+ * of distinct SM states than lanes, or more than 8 resident groups in a run;
+ * what that pass cannot finish goes to the simple simulator); -1 for a NULL
+ * handle.  Informational: results are exact either way, because the lists
+ * that carry abandoned items between the passes hold every item of the call
+ * (device memory: 16 bytes per work item, allocated by the call). */
 int64_t ko_last_fallback_items(const ko_gpu *g);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -207,7 +207,7 @@ ko_status fast_after_sync(ko_gpu *g)
     if (dc && cudaMemcpy(&cnt, dc, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess) return KO_ERR_CUDA;
     fs.d2h += sizeof(cnt);
     fs.last_overflow = cnt;
-    return cnt > (1ull << 20) ? KO_ERR_STATE : KO_OK;
+    return cnt > fs.ov_cap ? KO_ERR_STATE : KO_OK;  // cannot happen: the lists hold every item
 }
 
 }  // namespace

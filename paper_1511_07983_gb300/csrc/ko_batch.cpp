@@ -216,6 +216,7 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
     none.nchunks = 1;
     none.n_items = 0;
     none.levels = b->levels_max;  // the deepest launch of the batch sizes the node-state slab
+    none.reserve_items = std::max(b->n_ref_items, b->n_ex_items);  // and its longest one the item lists
     if (ko_fast_launch(&b->fast, none, b->slab, b->cap_stream) != KO_OK ||
         cudaStreamSynchronize(b->cap_stream) != cudaSuccess) {
         cudaGetLastError();
@@ -268,7 +269,7 @@ ko_status ko_batch_exec(ko_batch *b, ko_rank *out, uint64_t *hist, bool hist_dev
     const unsigned long long *dc = ko_fast_overflow_counter(&b->fast);
     if (dc && cudaMemcpy(cnt, dc, sizeof(cnt), cudaMemcpyDeviceToHost) == cudaSuccess)
         b->fast.last_overflow = cnt[0];
-    if (cnt[0] > (1ull << 20) || cnt[1] > (1ull << 20)) return KO_ERR_STATE;
+    if (cnt[0] > b->fast.ov_cap || cnt[1] > b->fast.ov_cap) return KO_ERR_STATE;  // cannot happen
     for (int i = 0; i < b->nsets; i++) {
         const KoAccum &a = b->h_accs[i];
         const long long mh = b->h_refs[i];

@@ -810,10 +810,9 @@ fast_kernel(KoWork a)
 // Device buffer layout inside KoFastState::buf.
 struct FastBuf {
     unsigned long long counter[2], ov_count[2], fb_counter, pad[3];
-    unsigned long long ov_list[1];   // kOvCap entries per pass
+    unsigned long long ov_list[1];   // KoFastState::ov_cap entries per pass
 };
 
-constexpr unsigned long long kOvCap = 1 << 20;
 constexpr size_t kFallbackScratch = size_t(256) << 20;
 
 
@@ -871,16 +870,28 @@ size_t ko_fast_smem_levels_cap() { return kMaxLevels; }
 
 ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaStream_t st)
 {
-    const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * 2 * kOvCap;
-    if (fs->cap < need) {
+    // a pass abandons an item at most once, so lists as long as the launch's work lose none
+    unsigned long long want = (unsigned long long)(w.n_items > w.reserve_items ? w.n_items : w.reserve_items);
+    want = ((want < 1024 ? 1024 : want) + 1023) & ~1023ull;
+    if (fs->ov_cap < want) {
+        // a stream being captured cannot take a free or a malloc: the caller
+        // must size the lists with an uncaptured launch first
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return KO_ERR_STATE;
+        }
+        const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * 2 * (size_t)want;
         cudaFree(fs->buf);
         fs->buf = nullptr;
         fs->cap = 0;
+        fs->ov_cap = 0;
         if (cudaMalloc(&fs->buf, need) != cudaSuccess) {
             cudaGetLastError();
             return KO_ERR_NOMEM;
         }
         fs->cap = need;
+        fs->ov_cap = want;
     }
     if (!fs->fb_scratch) {
         if (cudaMalloc(&fs->fb_scratch, kFallbackScratch) != cudaSuccess) {
@@ -919,7 +930,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w.run_limit = fs->run_limit;
     if (w.levels < 1) w.levels = 1;
     if (w.levels > kMaxLevels) w.levels = kMaxLevels;
-    w.ov_cap = kOvCap;
+    w.ov_cap = fs->ov_cap;
     // pass 1: all items, 8 group slots per run
     w.counter = &fb->counter[0];
     w.ov_count = &fb->ov_count[0];
@@ -941,7 +952,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w2.item_list = fb->ov_list;
     w2.item_count = &fb->ov_count[0];
     w2.ov_count = &fb->ov_count[1];
-    w2.ov_list = fb->ov_list + kOvCap;
+    w2.ov_list = fb->ov_list + fs->ov_cap;
     w2.run_limit = fs->run_limit;
     e = launch<32, kGWide, 32>(w2, st);
     if (e != cudaSuccess) {

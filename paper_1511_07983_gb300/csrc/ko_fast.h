@@ -41,12 +41,14 @@ struct KoWork {
     int run_limit;                    // runs one simulation may hold
     int *gstack;                      // non-null: DFS node states in this global slab, not shared memory
     long long gstack_words;           // words of gstack (bounds the segments that may use it)
+    long long reserve_items;          // sizing only: abandoned-item lists for this many items
 };
 
 // Device-side state of the run-length simulator, owned by a handle or batch.
 struct KoFastState {
-    void *buf = nullptr;        // counters and abandoned-item list
+    void *buf = nullptr;        // counters and the two passes' abandoned-item lists
     size_t cap = 0;
+    unsigned long long ov_cap = 0;  // entries of each abandoned-item list
     void *fb_scratch = nullptr; // fallback slabs
     size_t fb_bytes = 0;
     unsigned long long last_overflow = 0;
@@ -71,7 +73,10 @@ int ko_fast_d0(const KoFastState &fs, int n);
 
 // Enqueue one run-length launch over `w` (counters reset here) followed by the
 // device-side fallback for abandoned items.  Fills the counter fields of w.
-// Asynchronous, graph-capturable (no host synchronisation).
+// Asynchronous, graph-capturable (no host synchronisation) once an earlier
+// launch outside capture has sized the buffers: each abandoned-item list holds
+// max(w.n_items, w.reserve_items) entries, so no abandoned item is ever lost
+// (a pass abandons an item at most once).
 ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaStream_t st);
 
 // Device address of the count of items the first pass of the last launch
