@@ -79,6 +79,31 @@ def test_forced_handover_to_simple_simulator(ko, run_limit):
     assert np.array_equal(hist, st["hist"])
 
 
+def test_every_item_handed_over_on_a_large_launch(ko):
+    """More abandoned work items than any fixed list would hold: with one run
+    per simulation allowed and one saved level, all 1,814,400 items of an N=10
+    launch fail both run-length passes and reach the simple simulator; every
+    makespan must still arrive, equal to the default configuration's (itself
+    checked against the oracle on samples)."""
+    import torch
+    s = synth.gen_set("sets10", 3)
+    n_all = math.factorial(10)
+    with ko.Gpu.from_set(s) as g:
+        ref = torch.empty(n_all, dtype=torch.int64, device="cuda")
+        g.eval_all(ref)
+        torch.cuda.synchronize()
+    ids = synth.random_indices(31, n_all, 500)
+    assert np.array_equal(ref[torch.from_numpy(ids.astype(np.int64)).cuda()].cpu().numpy(),
+                          oracle.makespans_idx(s.gpu, s.kernels, idx=ids))
+    with ko.Gpu.from_set(s) as g:
+        g.configure(run_limit=1, levels=1)
+        out = torch.full((n_all,), -7, dtype=torch.int64, device="cuda")
+        g.eval_all(out)
+        torch.cuda.synchronize()
+        assert g.last_fallback_items() == n_all // 2 > (1 << 20)
+    assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("lanes", [16, 32])
 def test_single12_index_sample(ko, lanes):
     s = synth.gen_set("single12")
