@@ -38,6 +38,37 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def _declared_returns():
+    """name -> (return type, number of parameters) of every function in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for ret, name, args in re.findall(r"^([A-Za-z_][\w \*]*?)\b(ko_\w+)\s*\(([^)]*)\)", text, flags=re.M):
+            args = args.strip()
+            out[name] = (" ".join(ret.split()), 0 if args in ("", "void") else args.count(",") + 1)
+    return out
+
+
+def test_binding_declares_every_function_with_its_return_type():
+    """Every function of include/ko.h has a ctypes signature in the binding
+    whose return type and parameter count match the header's (a missing one
+    would default to a 32-bit int and truncate 64-bit results or pointers)."""
+    import ctypes
+
+    from paper_1511_07983_gb300 import ko as kmod
+    want = {"ko_status": ctypes.c_int32, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+            "double": ctypes.c_double, "void": None, "const char *": ctypes.c_char_p}
+    declared = _declared_returns()
+    assert set(declared) == set(kmod._SIGNATURES)
+    for name, (ret, nargs) in declared.items():
+        got, argtypes = kmod._SIGNATURES[name]
+        assert len(argtypes) == nargs, (name, nargs, len(argtypes))
+        if ret.endswith("*") and ret != "const char *":
+            assert got is ctypes.c_void_p, (name, ret)   # opaque handles
+        else:
+            assert got is want[ret], (name, ret, got)
+
+
 def test_library_exports_every_declared_symbol(ko):
     L = ko.lib()
     missing = [n for n in declared_functions() if not hasattr(L, n)]
