@@ -80,13 +80,14 @@ def test_forced_handover_to_simple_simulator(ko, run_limit):
 
 
 def test_every_item_handed_over_on_a_large_launch(ko):
-    """More abandoned work items than any fixed list would hold: with one run
-    per simulation allowed and one saved level, all 1,814,400 items of an N=10
-    launch fail both run-length passes and reach the simple simulator; every
-    makespan must still arrive, equal to the default configuration's (itself
-    checked against the oracle on samples)."""
+    """More abandoned work items than any fixed list would hold: ten one-block
+    kernels on a 2-SM GPU, one saved level (1,814,400 items of two orders) and
+    one run per simulation allowed.  Every item's first kernel cuts the single
+    run, so all items fail both run-length passes and reach the simple
+    simulator; every makespan must still arrive, equal to the default
+    configuration's (itself checked against the oracle on samples)."""
     import torch
-    s = synth.gen_set("sets10", 3)
+    s = synth.random_set(41, 10, gpu=(2, 65536, 49152, 64, 4), blk=(1, 1))
     n_all = math.factorial(10)
     with ko.Gpu.from_set(s) as g:
         ref = torch.empty(n_all, dtype=torch.int64, device="cuda")
