@@ -155,9 +155,10 @@ ko_status ko_heuristic_order_ex(ko_gpu *g, int32_t reading, int32_t *order_out);
  * Exactly one of idx / orders is non-NULL:
  *   idx     n Lehmer indices in [0, N!)   (N <= 20), host or device;
  *   orders  n x N kernel ids, row-major, each row a permutation, host or device.
- * A row that is not a permutation of 0..N-1 yields makespan -1.  Explicit
- * rows are asynchronous on `stream` when both pointers are device pointers;
- * index lists and host buffers synchronise `stream` before returning. */
+ * A row that is not a permutation of 0..N-1 (or an index >= N!) yields
+ * makespan -1.  Asynchronous on `stream` when the input and makespan_out are
+ * both device pointers; a host buffer on either side makes the call
+ * synchronise `stream` before returning. */
 ko_status ko_eval_orders(ko_gpu *g, const uint64_t *idx, const int8_t *orders, int64_t n,
                          int64_t *makespan_out, void *stream);
 
@@ -178,12 +179,16 @@ ko_status ko_eval_orders_ps(ko_gpu *g, const int8_t *orders, int64_t n, double *
  * the Algorithm 1 order.  If hist != NULL (host or device, nbins >= 1
  * entries) it receives the histogram with
  *     bin = floor((M - min) * nbins / (max - min + 1)).
- * Synchronises `stream`; `out` is host memory. */
+ * Synchronises `stream`; `out` is host memory.  The handle keeps the N!
+ * makespans on the device (8 bytes per order) for the histogram, and 16 bytes
+ * per work item for the lists that carry abandoned items between passes. */
 ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t *hist,
                         int32_t nbins, void *stream);
 
 /* Makespans of all N! orders in Lehmer-index order into makespans_out[N!]
- * (device memory), N <= 12.  Asynchronous on `stream`. */
+ * (device memory), N <= 12.  Asynchronous on `stream`; the handle holds 16
+ * bytes of device memory per work item (N! / (levels + 1)! items) for the
+ * lists that carry abandoned items between passes. */
 ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 
 /* Tuning knobs of the device simulators (set by the tuner; per handle).
