@@ -159,6 +159,57 @@ def _ptr(a):
     raise TypeError(f"unsupported buffer {type(a)}")
 
 
+def _is_tensor(a) -> bool:
+    return hasattr(a, "data_ptr") and not isinstance(a, np.ndarray)
+
+
+def _check_tensor(a, np_dtype, what):
+    import torch
+    want = {np.dtype(np.int8): (torch.int8,), np.dtype(np.int32): (torch.int32,),
+            np.dtype(np.int64): (torch.int64,), np.dtype(np.uint64): (torch.int64, torch.uint64),
+            np.dtype(np.float32): (torch.float32,), np.dtype(np.float64): (torch.float64,)}[np.dtype(np_dtype)]
+    if a.dtype not in want:
+        raise TypeError(f"{what}: expected a {want[0]} tensor, got {a.dtype}")
+    if not a.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+
+
+def _in_buf(a, np_dtype, what):
+    """An input buffer for the C ABI: host data becomes a C-contiguous numpy
+    array of np_dtype; a torch tensor must already have that element type."""
+    if _is_tensor(a):
+        _check_tensor(a, np_dtype, what)
+        return a
+    return np.ascontiguousarray(np.asarray(a, dtype=np_dtype))
+
+
+def _out_buf(a, np_dtype, what, min_len):
+    """An output buffer for the C ABI: never converted (a copy would lose the
+    results); element type, contiguity and length are checked."""
+    if _is_tensor(a):
+        _check_tensor(a, np_dtype, what)
+        n = a.numel()
+    elif isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(np_dtype):
+            raise TypeError(f"{what}: expected a {np.dtype(np_dtype)} array, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: array must be C-contiguous")
+        n = a.size
+    else:
+        raise TypeError(f"{what}: unsupported buffer {type(a)}")
+    if n < min_len:
+        raise ValueError(f"{what}: {n} elements, {min_len} needed")
+    return a
+
+
+def _rows(a, n, what):
+    """Rows of n kernel ids (int8), shape [count, n]."""
+    a = _in_buf(a, np.int8, what)
+    if len(a.shape) != 2 or a.shape[1] != n:
+        raise ValueError(f"{what}: expected shape [count, {n}], got {tuple(a.shape)}")
+    return a
+
+
 def _stream(stream):
     if stream is None:
         try:
@@ -218,11 +269,9 @@ def ko_set_sampling(g, mode):
 def ko_eval_orders_ps(g, orders, out=None, stream=None):
     """Processor-sharing makespans (float64) of rows of kernel ids (int8);
     numpy (host) or torch CUDA tensors."""
-    if isinstance(orders, np.ndarray) or not hasattr(orders, "data_ptr"):
-        orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int8))
-    n = orders.shape[0]
-    if out is None:
-        out = np.empty(n, dtype=np.float64)
+    orders = _rows(orders, ko_num_kernels(g), "orders")
+    n = int(orders.shape[0])
+    out = np.empty(n, dtype=np.float64) if out is None else _out_buf(out, np.float64, "out", n)
     _check(lib().ko_eval_orders_ps(g, _ptr(orders), n, _ptr(out), _stream(stream)), "ko_eval_orders_ps")
     return out
 
@@ -241,10 +290,15 @@ def ko_heuristic_order_ex(g, reading):
 def ko_eval_orders(g, idx=None, orders=None, out=None, stream=None):
     """Makespans of orders given as Lehmer indices (uint64) or rows of kernel
     ids (int8).  Inputs/outputs may be numpy (host) or torch CUDA tensors."""
+    if idx is not None:
+        idx = _in_buf(idx, np.uint64, "idx")
+        if len(idx.shape) != 1:
+            raise ValueError(f"idx: expected one dimension, got shape {tuple(idx.shape)}")
+    if orders is not None:
+        orders = _rows(orders, ko_num_kernels(g), "orders")
     src = idx if idx is not None else orders
     count = int(src.shape[0]) if src is not None else 0
-    if out is None:
-        out = np.empty(count, dtype=np.int64)
+    out = np.empty(count, dtype=np.int64) if out is None else _out_buf(out, np.int64, "out", count)
     _check(lib().ko_eval_orders(g, _ptr(idx), _ptr(orders), count, _ptr(out), _stream(stream)),
            "ko_eval_orders")
     return out
@@ -253,15 +307,25 @@ def ko_eval_orders(g, idx=None, orders=None, out=None, stream=None):
 def ko_rank_order(g, order=None, nbins=4096, hist=None, stream=None):
     """Exhaustive scoring; returns (ko_rank dict, histogram or None)."""
     r = ko_rank()
-    o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    o = None
+    if order is not None:
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        if o.shape != (ko_num_kernels(g),):
+            raise ValueError(f"order: expected {ko_num_kernels(g)} kernel ids, got shape {o.shape}")
     if hist is None and nbins:
         hist = np.zeros(nbins, dtype=np.uint64)
+    elif hist is not None:
+        hist = _out_buf(hist, np.uint64, "hist", int(nbins))
     _check(lib().ko_rank_order(g, _ptr(o), ctypes.byref(r), _ptr(hist), int(nbins) if hist is not None else 0,
                                _stream(stream)), "ko_rank_order")
     return r.as_dict(), hist
 
 
 def ko_eval_all(g, out, stream=None):
+    """All N! makespans into `out`, a CUDA int64 tensor of at least N! elements."""
+    if not _is_tensor(out):
+        raise TypeError("out: expected a CUDA int64 tensor")
+    _out_buf(out, np.int64, "out", math.factorial(ko_num_kernels(g)))
     return _check(lib().ko_eval_all(g, _ptr(out), _stream(stream)), "ko_eval_all")
 
 
@@ -319,7 +383,11 @@ def ko_batch_create(handles, nbins=0):
     return b
 
 
-def ko_batch_run(b, nsets, hist=None, stream=None):
+def ko_batch_run(b, nsets, hist=None, stream=None, nbins=0):
+    """Runs the batch; `hist`, if given, holds nsets x nbins uint64 (the bins
+    the batch was created with)."""
+    if hist is not None:
+        hist = _out_buf(hist, np.uint64, "hist", nsets * nbins)
     out = (ko_rank * nsets)()
     _check(lib().ko_batch_run(b, out, _ptr(hist), _stream(stream)), "ko_batch_run")
     return [r.as_dict() for r in out]
@@ -348,7 +416,7 @@ class Batch:
     def run(self, hist=None, stream=None):
         if hist is None and self.nbins:
             hist = np.zeros((self.nsets, self.nbins), dtype=np.uint64)
-        return ko_batch_run(self.b, self.nsets, hist=hist, stream=stream), hist
+        return ko_batch_run(self.b, self.nsets, hist=hist, stream=stream, nbins=self.nbins), hist
 
     def orders(self):
         return ko_batch_orders(self.b)
@@ -369,6 +437,23 @@ class Batch:
 
 
 KO_MODEL_PARAMS = 181249
+KO_MODEL_FEATURES = 192   # encoded width of one order (24 slots x 7 + 8 globals, padded)
+
+
+def _features(x):
+    """Host encoded orders, float32 [B, KO_MODEL_FEATURES]."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if x.ndim != 2 or x.shape[1] != KO_MODEL_FEATURES:
+        raise ValueError(f"x: expected shape [B, {KO_MODEL_FEATURES}], got {x.shape}")
+    return x
+
+
+def _targets(t, x):
+    """Host targets, float32 [B] for features x [B, ...]."""
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+    if t.shape != (x.shape[0],):
+        raise ValueError(f"t: expected shape ({x.shape[0]},), got {t.shape}")
+    return t
 
 
 class Model:
@@ -398,18 +483,18 @@ class Model:
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
-        assert flat.size == KO_MODEL_PARAMS
+        if flat.size != KO_MODEL_PARAMS:
+            raise ValueError(f"params: {flat.size} values, {KO_MODEL_PARAMS} expected")
         _check(lib().ko_model_set_params(self.m, _ptr(flat)), "ko_model_set_params")
 
     def predict(self, x, stream=None):
-        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+        x = _features(x)
         y = np.empty(x.shape[0], dtype=np.float32)
         _check(lib().ko_model_predict(self.m, _ptr(x), x.shape[0], _ptr(y), _stream(stream)), "ko_model_predict")
         return y
 
     def grad(self, x, t, stream=None):
-        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
-        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        x, t = _features(x), _targets(t, x)
         g = np.empty(KO_MODEL_PARAMS, dtype=np.float32)
         loss = ctypes.c_float()
         _check(lib().ko_model_grad(self.m, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss),
@@ -417,8 +502,7 @@ class Model:
         return g, loss.value
 
     def train_step(self, x, t, lr, stream=None):
-        x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
-        t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+        x, t = _features(x), _targets(t, x)
         loss = ctypes.c_float()
         _check(lib().ko_model_train_step(self.m, _ptr(x), _ptr(t), x.shape[0], lr, ctypes.byref(loss),
                                          _stream(stream)), "ko_model_train_step")
@@ -460,8 +544,8 @@ class Model:
 
 
 def ko_model_encode(g, orders, stream=None):
-    orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int8))
-    x = np.empty((orders.shape[0], 192), dtype=np.float32)
+    orders = _rows(np.asarray(orders), g.n, "orders")
+    x = np.empty((orders.shape[0], KO_MODEL_FEATURES), dtype=np.float32)
     _check(lib().ko_model_encode(g.h, _ptr(orders), orders.shape[0], _ptr(x), _stream(stream)), "ko_model_encode")
     return x
 

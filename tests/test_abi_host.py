@@ -110,6 +110,58 @@ def _sets():
     return out
 
 
+def test_binding_rejects_buffers_that_do_not_fit(ko):
+    """The C ABI takes pointers and counts only, so the binding checks what it
+    hands over: rows of N kernel ids, one-dimensional index lists, outputs of
+    the right element type and length.  A mismatch raises before any call."""
+    import torch
+    s = synth.gen_set("single8", 0)
+    n = s.n
+    with ko.Gpu.from_set(s) as g:
+        rows = np.zeros((2, n), dtype=np.int8)
+        ids = np.zeros(3, dtype=np.uint64)
+        for bad in (np.zeros((2, n - 1), dtype=np.int8), np.zeros(n, dtype=np.int8),
+                    np.zeros((2, n + 1), dtype=np.int8)):
+            with pytest.raises(ValueError):
+                g.eval_orders(orders=bad)
+            with pytest.raises(ValueError):
+                g.eval_orders_ps(bad)
+            with pytest.raises(ValueError):
+                ko.ko_model_encode(g, bad)
+        with pytest.raises(TypeError):
+            g.eval_orders(orders=torch.zeros((2, n), dtype=torch.int64))
+        with pytest.raises(ValueError):
+            g.eval_orders(idx=np.zeros((3, 1), dtype=np.uint64))
+        with pytest.raises(ValueError):
+            g.eval_orders(idx=ids, out=np.empty(2, dtype=np.int64))
+        with pytest.raises(TypeError):
+            g.eval_orders(idx=ids, out=np.empty(3, dtype=np.float64))
+        with pytest.raises(TypeError):
+            g.eval_orders(orders=rows, out=torch.empty(2, dtype=torch.float32))
+        with pytest.raises(TypeError):
+            g.eval_orders_ps(rows, out=np.empty(2, dtype=np.int64))
+        with pytest.raises(ValueError):
+            g.eval_orders_ps(rows, out=np.empty(1, dtype=np.float64))
+        with pytest.raises(ValueError):
+            g.rank_order(list(range(n - 1)), nbins=8)
+        with pytest.raises(ValueError):
+            g.rank_order(None, nbins=8, hist=np.zeros(7, dtype=np.uint64))
+        with pytest.raises(TypeError):
+            g.rank_order(None, nbins=8, hist=np.zeros(8, dtype=np.float64))
+        with pytest.raises(TypeError):
+            g.eval_all(np.empty(40320, dtype=np.int64))
+        with pytest.raises(ValueError):
+            g.eval_all(torch.empty(40319, dtype=torch.int64))
+        with pytest.raises(TypeError):
+            g.eval_all(torch.empty(40320, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        ko._features(np.zeros((4, ko.KO_MODEL_FEATURES - 1), dtype=np.float32))
+    with pytest.raises(ValueError):
+        ko._targets(np.zeros(3, dtype=np.float32), np.zeros((4, ko.KO_MODEL_FEATURES)))
+    with pytest.raises(ValueError):
+        ko._out_buf(np.zeros((2, 3), dtype=np.uint64), np.uint64, "hist", 2 * 4)
+
+
 def test_heuristic_matches_oracle(ko):
     for s in _sets():
         with ko.Gpu.from_set(s) as g:
