@@ -6,11 +6,14 @@
 // * Runs.  SMs with identical state (usage, SumC, SumM and resident groups
 //   with identical end times) form a run of consecutive SM indices.  One lane
 //   of a LANES-wide segment (16 or 32 lanes of a warp) holds one run in
-//   registers.  The two 16-lane segments of a warp take consecutive work items
-//   and step through their events together, with whole-warp collectives and
-//   per-segment predicates, so they share instructions where their paths agree.  Runs are split only where SMs of a run receive different
+//   registers.  Runs are split only where SMs of a run receive different
 //   numbers of blocks; the number of runs stays small because the round-robin
 //   dispatch treats consecutive SMs alike.
+// * Two simulations per warp.  The two 16-lane segments of a warp take two
+//   work items whose prefixes differ only in the order of their last two
+//   kernels and step through their events together, with whole-warp
+//   collectives and per-segment predicates, so they share instructions where
+//   their paths agree.
 // * Bulk round-robin.  Placing the head kernel is a water-fill: each SM of
 //   run j takes at most cap_j more blocks (min over the four limits), sweeps go
 //   cyclically from the round-robin pointer p and give one block to every SM
@@ -23,14 +26,16 @@
 //   every live end lies within (t, t + max duration] and the host only uses
 //   this path when every duration is below 2^31, so comparisons are exact.
 // * Prefix sharing.  The lexicographic order of Lehmer indices is a DFS over
-//   kernel choices; the state after placing a prefix is saved in shared memory
-//   and restored for each sibling, so each order only pays for the kernels in
+//   kernel choices; the state after placing a prefix is saved (in a per-segment
+//   global slab that stays in L2, or in shared memory) and restored for each
+//   sibling, so each order only pays for the kernels in
 //   which it differs from its predecessor (about e kernels per order).
 //   The state at a DFS node is "prefix placed, current burst still open":
 //   the next kernel continues the same burst.
 // * Overflow.  A segment that would need more runs than lanes, or more than
-//   kG groups in one run, abandons its work item and records it; the host
-//   re-runs recorded items with the simple simulator.
+//   kG groups in one run, abandons its work item and records it; a second
+//   pass with 32 lanes and 16 group slots re-runs the recorded items, and the
+//   simple simulator takes whatever that pass abandons, all on the stream.
 #include "ko_fast.h"
 
 namespace {
