@@ -5,6 +5,11 @@
 // ordered kernel descriptors (not part of the paper: a proposal generator for
 // sets too large to enumerate, whose proposals are rescored exactly).
 //
+// The GEMMs here are the warp-level mma.sync path; the tcgen05 kernels of
+// ko_mlp_tc.cu run every GEMM whose sizes their tiles divide, and these take
+// the rest (batches that are not multiples of 128, or 256 for weight
+// gradients) and serve as the cross-check in tests.
+//
 // GEMM form used everywhere ("NT"): C[m][n] = sum_k A[m][k] * B[n][k], both
 // operands K-contiguous BF16 in global memory.  Forward layers take
 // B = W^T (stored n-major), input gradients take B = W (k-major), weight

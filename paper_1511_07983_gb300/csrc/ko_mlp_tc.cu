@@ -13,6 +13,8 @@
 //                          split-K, one 256-wide K slice per CTA, FP32 partial
 //                          tiles to a workspace; wgrad_reduce_kernel sums the
 //                          slices in a fixed order (deterministic).
+//   tc_tma_kernel          the MODE 0 layer with both operands loaded by TMA
+//                          (cp.async.bulk.tensor), the default for inference.
 //
 //  * Operands sit in shared memory in the no-swizzle core-matrix layout: a
 //    core matrix is 8 rows x 16 bytes; core matrices adjacent along K are
