@@ -117,3 +117,23 @@ def test_pair_order_is_a_bijection_of_swap_partners(n, d0):
             if j % 2 == 0 and g0 >= lo and g0 + M <= hi:
                 a, b = prefix(n, d0, img[j - lo]), prefix(n, d0, img[j + 1 - lo])
                 assert a[:-2] == b[:-2] and a[-2:] == b[-2:][::-1]
+
+
+def test_header_limits_fit_the_packed_fields():
+    """The run-length simulator packs state into fixed bit fields; the ABI's
+    limits must keep every packed value in range."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "ko.h")).read()
+    lim = {}
+    for name, num, shift in re.findall(r"#define (KO_MAX_\w+) (?:(\d+)|\(1 << (\d+)\))", text):
+        lim[name] = int(num) if num else 1 << int(shift)
+    max_kernels, max_sm, max_blk, max_cycles = (lim["KO_MAX_KERNELS"], lim["KO_MAX_SM"],
+                                                lim["KO_MAX_BLK_SM"], lim["KO_MAX_CYCLES"])
+    assert max_kernels <= 32                  # kernel id: 5 bits of a group word
+    assert max_blk <= 63                      # blocks per SM of a group: 6 bits
+    assert max_sm < 1 << 16                   # run range: begin | count << 16
+    assert max_cycles < 1 << 25 and max_blk < 1 << 7   # warps used | blocks used << 25
+    assert max_blk * max_cycles < 1 << 31     # SumC, SumM of one SM in a 32-bit int
+    assert max_cycles * max(max_blk * max_cycles, 1 << 30) + (1 << 30) < 1 << 64  # duration product
