@@ -137,3 +137,32 @@ def test_header_limits_fit_the_packed_fields():
     assert max_cycles < 1 << 25 and max_blk < 1 << 7   # warps used | blocks used << 25
     assert max_blk * max_cycles < 1 << 31     # SumC, SumM of one SM in a 32-bit int
     assert max_cycles * max(max_blk * max_cycles, 1 << 30) + (1 << 30) < 1 << 64  # duration product
+
+
+def test_float_reciprocal_quotient_with_one_correction_is_exact():
+    """The per-SM capacity uses floor(x / d) for 0 <= x <= 2^24, d >= 1,
+    clamped at 32: min(x, 32 d) times the float reciprocal of d (IEEE
+    round-to-nearest conversion, reciprocal and product, truncation), then one
+    exact integer correction either way.  Checked where it is hardest, on both
+    sides of every integer quotient 0..32, for every d up to 2^12 and random
+    larger d."""
+    import numpy as np
+
+    def quot32(x, d):
+        xc = np.minimum(x, d << 5)
+        rcp = (np.float32(1.0) / d.astype(np.float32)).astype(np.float32)
+        q = np.trunc(xc.astype(np.float32) * rcp).astype(np.int64)
+        q = q + ((q + 1) * d <= xc)
+        q = q - (q * d > xc)
+        return q
+
+    rng = np.random.default_rng(5)
+    ds = np.concatenate([np.arange(1, 1 << 12), rng.integers(1 << 12, 1 << 24, 20000)]).astype(np.int64)
+    k = np.arange(0, 34, dtype=np.int64)
+    for off in (-1, 0, 1):
+        d = np.repeat(ds, k.size)
+        x = np.clip(np.tile(k, ds.size) * d + off, 0, 1 << 24)
+        assert np.array_equal(quot32(x, d), np.minimum(x // d, 32))
+    x = rng.integers(0, (1 << 24) + 1, 200000)
+    d = rng.integers(1, 1 << 24, 200000)
+    assert np.array_equal(quot32(x, d), np.minimum(x // d, 32))
