@@ -462,6 +462,18 @@ ko_status ko_hw_device_limits(int32_t out[7]);
 /* Registers per thread of the busy kernel of `kind` (cudaFuncGetAttributes). */
 ko_status ko_hw_regs(int32_t kind, int32_t *regs_per_thread);
 
+/* Integer issue-rate microbenchmark (the denominator of the simulators'
+ * integer roofline; not part of the paper).  Fills every SM of the current
+ * device with 256-thread blocks whose threads each run 8 independent chains of
+ * 32-bit add, xor and min (one instruction each, register operands only) for
+ * `turns` (1..2^20) loop turns of 16 steps, and times the launch with CUDA
+ * events on the legacy default stream (one warm-up launch, then the fastest of
+ * three).  *lane_ops receives the thread-level integer operations one launch
+ * executes (threads x turns x 384), *ms_out its time in milliseconds; the
+ * rate is lane_ops / ms.  Allocates and frees a small device buffer;
+ * synchronises the device's default stream. */
+ko_status ko_hw_int_peak(int32_t turns, int64_t *lane_ops, float *ms_out);
+
 /* Times `count` launch orders (host, count x n kernel ids, row-major): for
  * each order, `reps` runs (1..64) that launch kernel order[j] on stream j in
  * host order j = 0..n-1 between a start event and a stop event that waits for

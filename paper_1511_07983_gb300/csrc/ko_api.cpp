@@ -266,6 +266,8 @@ int32_t ko_add_kernel(ko_gpu *g, int32_t n_reg_i, int32_t n_shm_i, int32_t n_war
     KoKern &k = g->h.k[g->h.n];
     k.r = n_reg_i; k.s = n_shm_i; k.w = n_warp_i; k.b = n_tblk_i;
     k.c = (int32_t)c_i; k.m = (int32_t)m_i;
+    g->h.lk[g->h.n] = KoLaneK{(uint32_t)n_reg_i | (1u << 19) | ((uint32_t)n_warp_i << 25), (uint32_t)n_shm_i,
+                              (uint32_t)c_i, (uint32_t)m_i};
     int64_t lb, ub;
     g->h.n++;
     if (!ko_bounds_host(g->h, &lb, &ub)) {
@@ -602,7 +604,7 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
     if (!g) return fail(KO_ERR_ARG);
     switch (key) {
     case KO_OPT_LANES:
-        if (value != 16 && value != 32) return fail(KO_ERR_ARG);
+        if (value != 1 && value != 16 && value != 32) return fail(KO_ERR_ARG);
         g->fast.lanes = (int)value;
         break;
     case KO_OPT_LEVELS:
@@ -853,6 +855,13 @@ ko_status ko_hw_regs(int32_t kind, int32_t *regs_per_thread)
     if (s) return fail(s);
     *regs_per_thread = r;
     return ok();
+}
+
+ko_status ko_hw_int_peak(int32_t turns, int64_t *lane_ops, float *ms_out)
+{
+    if (!lane_ops || !ms_out || turns < 1 || turns > (1 << 20)) return fail(KO_ERR_ARG);
+    ko_status s = ko_hw_int_peak_impl(turns, lane_ops, ms_out);
+    return s ? fail(s) : ok();
 }
 
 ko_status ko_hw_time_orders(ko_hw *h, const int8_t *orders, int64_t count, int32_t reps, float *ms_out)

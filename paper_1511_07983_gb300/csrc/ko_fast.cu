@@ -814,7 +814,7 @@ fast_kernel(KoWork a)
 
 // Device buffer layout inside KoFastState::buf.
 struct FastBuf {
-    unsigned long long counter[2], ov_count[2], fb_counter, pad[3];
+    unsigned long long counter[3], ov_count[3], fb_counter, pad[1];
     unsigned long long ov_list[1];   // KoFastState::ov_cap entries per pass
 };
 
@@ -886,7 +886,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
             cudaGetLastError();
             return KO_ERR_STATE;
         }
-        const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * 2 * (size_t)want;
+        const size_t need = sizeof(FastBuf) + sizeof(unsigned long long) * 3 * (size_t)want;
         cudaFree(fs->buf);
         fs->buf = nullptr;
         fs->cap = 0;
@@ -904,6 +904,26 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
             return KO_ERR_NOMEM;
         }
         fs->fb_bytes = kFallbackScratch;
+    }
+    const bool lane = fs->lanes == 1;
+    if (lane) {
+        // one-thread-per-order pass: a node-state slab for every thread it runs
+        const size_t need = ko_lane_slab_bytes(w.levels < 1 ? 1 : w.levels);
+        if (fs->lslab_bytes < need) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+                cudaGetLastError();
+                return KO_ERR_STATE;
+            }
+            cudaFree(fs->lslab);
+            fs->lslab = nullptr;
+            fs->lslab_bytes = 0;
+            if (cudaMalloc(&fs->lslab, need) != cudaSuccess) {
+                cudaGetLastError();
+                return KO_ERR_NOMEM;
+            }
+            fs->lslab_bytes = need;
+        }
     }
     if (fs->stack_global) {
         // pass 1: at most 8 blocks of 8 segments per SM, 16 saved lanes per level
@@ -936,15 +956,33 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     if (w.levels < 1) w.levels = 1;
     if (w.levels > kMaxLevels) w.levels = kMaxLevels;
     w.ov_cap = fs->ov_cap;
-    // pass 1: all items, 8 group slots per run
-    w.counter = &fb->counter[0];
-    w.ov_count = &fb->ov_count[0];
-    w.ov_list = fb->ov_list;
     w.item_list = nullptr;
     w.item_count = nullptr;
+    int list = 0;  // abandoned-item list the next pass writes
+    cudaError_t e = cudaSuccess;
+    if (lane) {
+        // pass 0: all items, one simulation per thread
+        KoWork w0 = w;
+        w0.counter = &fb->counter[2];
+        w0.ov_count = &fb->ov_count[0];
+        w0.ov_list = fb->ov_list;
+        w0.gstack = (int *)fs->lslab;
+        w0.gstack_words = (long long)(fs->lslab_bytes / sizeof(int));
+        if ((e = ko_launch_lane(w0, st)) != cudaSuccess) {
+            cudaGetLastError();
+            return KO_ERR_CUDA;
+        }
+        w.item_list = fb->ov_list;
+        w.item_count = &fb->ov_count[0];
+        list = 1;
+    }
+    // pass 1: all items (or those pass 0 abandoned), 16 lanes per run-length simulation, 8 group slots
+    w.counter = &fb->counter[0];
+    w.ov_count = &fb->ov_count[list];
+    w.ov_list = fb->ov_list + list * fs->ov_cap;
     w.gstack = fs->stack_global ? (int *)fs->gstack : nullptr;
     w.gstack_words = fs->stack_global ? (long long)(fs->gstack_bytes / sizeof(int)) : 0;
-    cudaError_t e = fs->lanes == 16 ? launch<16, kG, 16>(w, st) : launch<32, kG, 16>(w, st);
+    e = fs->lanes == 32 ? launch<32, kG, 16>(w, st) : launch<16, kG, 16>(w, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_CUDA;
@@ -954,10 +992,10 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     w2.gstack = nullptr;  // the wide pass keeps its (32-lane) node states in shared memory
     w2.gstack_words = 0;
     w2.counter = &fb->counter[1];
-    w2.item_list = fb->ov_list;
-    w2.item_count = &fb->ov_count[0];
-    w2.ov_count = &fb->ov_count[1];
-    w2.ov_list = fb->ov_list + fs->ov_cap;
+    w2.item_list = fb->ov_list + list * fs->ov_cap;
+    w2.item_count = &fb->ov_count[list];
+    w2.ov_count = &fb->ov_count[list + 1];
+    w2.ov_list = fb->ov_list + (list + 1) * fs->ov_cap;
     w2.run_limit = fs->run_limit;
     e = launch<32, kGWide, 32>(w2, st);
     if (e != cudaSuccess) {
@@ -990,6 +1028,9 @@ void ko_fast_release(KoFastState *fs)
     cudaFree(fs->gstack);
     fs->gstack = nullptr;
     fs->gstack_bytes = 0;
+    cudaFree(fs->lslab);
+    fs->lslab = nullptr;
+    fs->lslab_bytes = 0;
     fs->buf = nullptr;
     fs->fb_scratch = nullptr;
     fs->cap = 0;

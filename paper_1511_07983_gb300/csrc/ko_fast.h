@@ -52,13 +52,16 @@ struct KoFastState {
     void *fb_scratch = nullptr; // fallback slabs
     size_t fb_bytes = 0;
     unsigned long long last_overflow = 0;
-    int lanes = 16;             // lanes per simulation (16 or 32)
+    int lanes = 16;             // lanes per simulation: 1 (one thread per order, then the run-length
+                                // passes over what it abandons), 16 or 32
     int levels = 4;             // saved DFS levels (items fix N - 1 - levels kernels)
     bool disabled = false;      // use the simple simulator only
     int run_limit = 32;         // cap on runs per simulation (tests force the hand-over)
     int stack_global = 1;       // DFS node states in global memory (1) or shared memory (0)
     void *gstack = nullptr;     // global slab for node states
     size_t gstack_bytes = 0;
+    void *lslab = nullptr;      // node-state slab of the one-thread-per-order pass
+    size_t lslab_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last run-length launch
     double last_ms = -1.0;
     long long h2d = 0, d2h = 0;
@@ -78,6 +81,12 @@ int ko_fast_d0(const KoFastState &fs, int n);
 // max(w.n_items, w.reserve_items) entries, so no abandoned item is ever lost
 // (a pass abandons an item at most once).
 ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaStream_t st);
+
+// One-thread-per-order pass (ko_lane.cu) over the items of `w` (counters and
+// the abandoned-item list already set; w.gstack = its node-state slab of
+// ko_lane_slab_bytes(w.levels) bytes).
+cudaError_t ko_launch_lane(const KoWork &w, cudaStream_t st);
+size_t ko_lane_slab_bytes(int levels);
 
 // Device address of the count of items the first pass of the last launch
 // abandoned (followed by the count the wide second pass abandoned).

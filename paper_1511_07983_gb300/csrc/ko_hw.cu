@@ -296,3 +296,82 @@ ko_status ko_hw_time_grid_impl(ko_hw *h, int k, int blocks, int reps, float *ms_
     *ms_out = best;
     return KO_OK;
 }
+
+// ------------------------------------------------------------ integer peak
+// Issue-rate microbenchmark of the plain integer ALU path: every thread runs 8
+// independent chains of (add, xor, min) on 32-bit registers, 16 steps per loop
+// turn, each step one PTX instruction; the chains keep every scheduler's issue
+// slot fed from register operands alone.  The result is the denominator of the
+// simulators' integer roofline (lane-operations per second).
+namespace {
+
+constexpr int kPeakThreads = 256;
+constexpr int kPeakChains = 8;
+constexpr int kPeakUnroll = 16;
+constexpr long long kPeakOpsPerTurn = 3ll * kPeakChains * kPeakUnroll;
+
+__global__ void __launch_bounds__(kPeakThreads) int_peak_kernel(uint32_t *sink, uint32_t s0, int turns)
+{
+    uint32_t a[kPeakChains];
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) a[c] = s0 * (threadIdx.x + 1u) + (uint32_t)c * 0x9e3779b9u;
+    const uint32_t b = s0 | 1u, x = s0 ^ 0xa5a5a5a5u, m = 0xfffffff0u ^ s0;
+    for (int i = 0; i < turns; i++) {
+#pragma unroll
+        for (int u = 0; u < kPeakUnroll; u++) {
+#pragma unroll
+            for (int c = 0; c < kPeakChains; c++) {
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a[c]) : "r"(b));
+                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a[c]) : "r"(x));
+                asm volatile("min.u32 %0, %0, %1;" : "+r"(a[c]) : "r"(m));
+            }
+        }
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) r ^= a[c];
+    if (r == s0) sink[blockIdx.x * kPeakThreads + threadIdx.x] = r;  // keeps the result observable
+}
+
+}  // namespace
+
+ko_status ko_hw_int_peak_impl(int32_t turns, int64_t *lane_ops, float *ms_out)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, int_peak_kernel, kPeakThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_CUDA;
+    }
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
+    uint32_t *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ko_status st = KO_OK;
+    if (cudaMalloc(&sink, sizeof(uint32_t) * (size_t)blocks * kPeakThreads) != cudaSuccess) {
+        cudaGetLastError();
+        return KO_ERR_NOMEM;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = KO_ERR_CUDA;
+    float best = 0.0f;
+    for (int rep = 0; st == KO_OK && rep < 4; rep++) {  // the first run warms up; the fastest of the rest counts
+        cudaEventRecord(e0, 0);
+        int_peak_kernel<<<blocks, kPeakThreads>>>(sink, 0x1234567u + (uint32_t)rep, rep == 0 ? 16 : turns);
+        ko_count_launch();
+        cudaEventRecord(e1, 0);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            st = KO_ERR_CUDA;
+        else if (rep > 0 && (best == 0.0f || ms < best))
+            best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaGetLastError();
+    if (st) return st;
+    *lane_ops = (int64_t)blocks * kPeakThreads * turns * kPeakOpsPerTurn;
+    *ms_out = best;
+    return KO_OK;
+}
+

@@ -14,6 +14,13 @@ struct KoKern {
     int32_t r, s, w, b, c, m;
 };
 
+// Packed per-kernel record of the one-thread-per-order simulator (ko_lane.cu):
+// one block's share of its usage word (registers | 1 << 19 | warps << 25;
+// meaningful when N_reg_SM < 2^19 and N_warp_SM < 128), shared memory, c, m.
+struct KoLaneK {
+    uint32_t pk, s, c, m;
+};
+
 // Device-side description of one kernel set on one simulated GPU.
 struct KoSet {
     int32_t n;                   // kernels in the set
@@ -24,6 +31,7 @@ struct KoSet {
     int32_t pad0;
     int64_t ref_makespan;        // makespan the exhaustive counts compare against
     KoKern k[KO_MAX_KERNELS];
+    KoLaneK lk[KO_MAX_KERNELS];  // the same kernels, packed (16-byte aligned: KoKern table is 576 bytes)
 };
 
 // Exhaustive accumulators of one set (device memory).
@@ -118,6 +126,7 @@ ko_status ko_hw_time_impl(ko_hw *h, const int8_t *orders, long long count, int r
 ko_status ko_hw_time_grid_impl(ko_hw *h, int k, int blocks, int reps, float *ms_out);
 ko_status ko_hw_trace_impl(ko_hw *h, const int8_t *ord, unsigned long long *rec_out, float *ms_out);
 long long ko_hw_trace_blocks(const ko_hw *h);
+ko_status ko_hw_int_peak_impl(int32_t turns, int64_t *lane_ops, float *ms_out);
 ko_status ko_local_search_set(KoFastState *fs, const KoSet &h, const int32_t *start, bool moves, int max_iters,
                               int32_t *order_out, int64_t *makespan_out, int32_t *steps_out, int64_t *evals_out,
                               double *gpu_ms, cudaStream_t st);

@@ -100,6 +100,8 @@ _SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "ko_hw_create": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
     "ko_hw_regs": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "ko_hw_int_peak": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "ko_hw_device_limits": (ctypes.c_int32, [ctypes.c_void_p]),
     "ko_hw_time_orders": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.c_void_p]),
@@ -587,6 +589,15 @@ def ko_hw_device_limits():
     out = np.zeros(7, dtype=np.int32)
     _check(lib().ko_hw_device_limits(_ptr(out)), "ko_hw_device_limits")
     return tuple(int(v) for v in out)
+
+
+def ko_hw_int_peak(turns=2048):
+    """(lane operations per launch, fastest launch time in ms) of the integer
+    issue-rate microbenchmark on the current device."""
+    ops = ctypes.c_int64()
+    ms = ctypes.c_float()
+    _check(lib().ko_hw_int_peak(int(turns), ctypes.byref(ops), ctypes.byref(ms)), "ko_hw_int_peak")
+    return int(ops.value), float(ms.value)
 
 
 def ko_hw_regs(kind):

@@ -1,0 +1,140 @@
+"""GPU parity of the one-thread-per-order simulator (KO_OPT_LANES = 1): every
+makespan, count and histogram equals the oracle's, for every prefix depth, for
+explicit and index lists, and when work items overflow a simulation's runs or
+group slots and move on to the run-length passes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_07983_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ko():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1511_07983_gb300 import build, ko as kmod
+    build.build()
+    torch.cuda.init()
+    return kmod
+
+
+def _all(g, n):
+    import torch
+    out = torch.full((math.factorial(n),), -7, dtype=torch.int64, device="cuda")
+    g.eval_all(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2, 3, 4, 5, 6])
+def test_single8_all_orders_every_depth(ko, levels):
+    s = synth.gen_set("single8")
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=40320)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1, levels=levels)
+        assert np.array_equal(_all(g, 8), want)
+        assert g.last_fallback_items() == 0
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_sets_exhaustive(ko, seed):
+    # tiny and large N_SM, power-of-two and odd capacities, one-block SMs, heavy smem
+    n = 3 + seed % 6
+    gpus = [(13, 65536, 49152, 64, 16), (148, 65536, 233472, 64, 32), (7, 32768, 49152, 48, 8),
+            (40, 65536, 98304, 64, 32), (5, 65536, 233472, 64, 1)]
+    gpu = gpus[seed % len(gpus)]
+    caps = (32768, 32768) if seed % 3 else (3000, 7001)
+    s = synth.random_set(200 + seed, n, gpu=gpu, blk=(1, 5 * gpu[0]), c=(100, 30000),
+                         c_cap=caps[0], m_cap=caps[1])
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=math.factorial(n))
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1)
+        got = _all(g, n)
+    assert np.array_equal(got, want), int(np.argmax(got != want))
+
+
+@pytest.mark.parametrize("run_limit", [1, 2, 4, 8])
+def test_overflowing_items_move_to_the_run_length_passes(ko, run_limit):
+    """A run limit below what the orders need makes the first pass abandon
+    items; the run-length and simple passes must finish them exactly, and the
+    reductions must count every order once."""
+    s = synth.gen_set("sets10", 3, n=7)
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=5040)
+    h = oracle.heuristic(s.gpu, s.kernels)
+    st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h), makespans=want)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1, run_limit=run_limit)
+        assert np.array_equal(_all(g, 7), want)
+        if run_limit <= 2:
+            assert g.last_fallback_items() > 0
+        r, hist = g.rank_order(h, nbins=4096)
+    assert (r["min"], r["max"], r["n_better"], r["n_equal"], r["n_worse"]) == \
+        (st["min"], st["max"], st["n_better"], st["n_equal"], st["n_worse"])
+    assert np.array_equal(hist, st["hist"])
+
+
+def test_index_and_row_lists(ko):
+    s = synth.gen_set("single12")
+    ids = synth.random_indices(91, math.factorial(12), 3000)
+    rows = synth.random_orders(92, 12, 500).astype(np.int8)
+    bad = rows[:3].copy()
+    bad[0, 0] = bad[0, 1]            # repeated kernel
+    bad[1, 5] = 12                   # out of range
+    bad[2, 3] = -1
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1)
+        got_i = g.eval_orders(idx=ids)
+        got_r = g.eval_orders(orders=rows)
+        got_b = g.eval_orders(orders=np.concatenate([bad, rows[:5]]))
+    assert np.array_equal(got_i, oracle.makespans_idx(s.gpu, s.kernels, idx=ids))
+    assert np.array_equal(got_r, oracle.makespans_orders(s.gpu, s.kernels, rows.astype(np.int32)))
+    assert list(got_b[:3]) == [-1, -1, -1]
+    assert np.array_equal(got_b[3:], got_r[:5])
+
+
+def test_single12_subspace_by_prefix(ko):
+    """Every order of several N=12 prefix subtrees (the bench set, 148 SMs):
+    the stored makespans of whole work items against the oracle one by one."""
+    import torch
+    s = synth.gen_set("single12")
+    n_all = math.factorial(12)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1, levels=5)
+        out = torch.empty(n_all, dtype=torch.int64, device="cuda")
+        g.eval_all(out)
+        torch.cuda.synchronize()
+        # a few items need more runs or group slots than one simulation holds
+        # and are finished by the run-length passes
+        assert g.last_fallback_items() < n_all // math.factorial(6) // 1000
+    per = math.factorial(6)
+    for item in (0, 1, 12345, n_all // per // 2, n_all // per - 1):
+        got = out[item * per:(item + 1) * per].cpu().numpy()
+        want = oracle.makespans_idx(s.gpu, s.kernels, first=item * per, count=per)
+        assert np.array_equal(got, want), item
+    ids = synth.random_indices(93, n_all, 3000).astype(np.int64)
+    got = out[torch.from_numpy(ids).cuda()].cpu().numpy()
+    assert np.array_equal(got, oracle.makespans_idx(s.gpu, s.kernels, idx=ids.astype(np.uint64)))
+
+
+@pytest.mark.parametrize("case", ["one_block_per_sm", "no_smem", "bk32_tiny_sm", "single_kernel", "two_kernels"])
+def test_edge_sets(ko, case):
+    if case == "one_block_per_sm":
+        s = synth.random_set(51, 6, gpu=(7, 65536, 233472, 64, 1), blk=(1, 30))
+    elif case == "no_smem":
+        s = synth.random_set(52, 6, gpu=(13, 65536, 49152, 64, 16), blk=(5, 80))
+        s.kernels[:, 1] = 0
+    elif case == "bk32_tiny_sm":
+        s = synth.random_set(53, 6, gpu=(2, 65536, 233472, 64, 32), blk=(1, 40))
+    elif case == "single_kernel":
+        s = synth.random_set(54, 1, gpu=(148, 65536, 233472, 64, 32), blk=(100, 1000))
+    else:
+        s = synth.random_set(55, 2, gpu=(148, 65536, 233472, 64, 32), blk=(100, 1000))
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=math.factorial(s.n))
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1)
+        assert np.array_equal(_all(g, s.n), want), case
