@@ -418,7 +418,14 @@ void ko_model_destroy(ko_model *m);
  * KO_ERR_TOO_LARGE.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and uses it as
+ * before any stream capture.  The CUDA runtime reserves the array on a device
+ * when it loads this library's device code there (by default at the
+ * library's first use on that device), so make the library's first call on a
+ * device before another allocator reserves that device's memory: if the
+ * reservation fails, calls return KO_ERR_CUDA.  The address is kept per
+ * device index for the life of the process; after cudaDeviceReset it is
+ * stale, so do not call this entry point again on a device that was reset.
+ * Every call shares the one array and uses it as
  * scratch only (nothing carries over between calls), so calls that overlap
  * on the GPU -- concurrent streams, or other host threads -- race on it:
  * serialise them.  Asynchronous on `stream`. */

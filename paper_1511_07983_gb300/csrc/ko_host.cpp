@@ -177,7 +177,10 @@ bool ko_bounds_host(const KoSet &h, int64_t *lb, int64_t *ub)
     low = std::max(low, div_up(area_reg, (__int128)h.S * h.R));
     if (uses_shm) low = std::max(low, div_up(area_shm, (__int128)h.S * h.Sh));
     *lb = h.n > 0 ? low : 0;
+    // the bound itself saturates only where int64 ends; sets whose bound
+    // reaches 2^62 are refused, which keeps every simulated clock far from
+    // overflow
     const __int128 limit = (__int128)1 << 62;
-    *ub = serial >= limit ? INT64_MAX : (int64_t)serial;
+    *ub = serial > (__int128)INT64_MAX ? INT64_MAX : (int64_t)serial;
     return serial < limit;
 }

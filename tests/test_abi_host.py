@@ -202,6 +202,30 @@ def test_bounds_match_oracle(ko):
             assert g.bounds() == oracle.bounds(s.gpu, s.kernels)
 
 
+def test_upper_bound_at_the_admission_limit(ko):
+    """Sets are admitted while the serial upper bound stays below 2^62: one
+    kernel of 2^17 - 1 blocks with c = m = 2^20 on a 32-slot SM with unit
+    capacities has UB = (2^17 - 1) * 2^20 * 32 * 2^20 = 2^62 - 2^45, which
+    the library reports exactly as the oracle does; one more block of the same
+    kind makes UB = 2^62, which the oracle computes exactly and the library
+    refuses (KO_ERR_OVERFLOW).  Above int64 the oracle saturates."""
+    gpu = (4, 65536, 49152, 64, 32, 1, 1)
+    big = [1, 0, 1, (1 << 17) - 1, 1 << 20, 1 << 20]
+    g = ko.Gpu(*gpu[:5], c_cap=1, m_cap=1)
+    g.add_kernel(*big)
+    lb, ub = g.bounds()
+    assert ub == (1 << 62) - (1 << 45)
+    assert (lb, ub) == oracle.bounds(gpu, [big])
+    one = [1, 0, 1, 1, 1 << 20, 1 << 20]
+    assert oracle.bounds(gpu, [big, one])[1] == 1 << 62
+    with pytest.raises(ko.KoError) as e:
+        g.add_kernel(*one)
+    assert "OVERFLOW" in str(e.value)
+    assert g.bounds() == (lb, ub)   # the refused kernel left the set unchanged
+    huge = [1, 0, 1, 1 << 20, 1 << 24, 1 << 24]
+    assert oracle.bounds(gpu, [huge])[1] == (1 << 63) - 1
+
+
 def test_non_power_of_two_capacity_heuristic(ko):
     s = synth.random_set(5, 9, blk=(1, 100), c_cap=3000, m_cap=7000)
     with ko.Gpu.from_set(s) as g:
