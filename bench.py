@@ -156,11 +156,39 @@ def measured_traffic(workload):
     mh = re.search(r"^- source sha256 \(ko_fast.cu \+ ko_fast.h\): ([0-9a-f]{64})$", text, re.M)
     if not mb or not mh:
         return None
+    return int(mb.group(1)) if source_hash() == mh.group(1) else None
+
+
+def measured_counters(workload):
+    """Issue-slot use, active threads per instruction and warp instructions
+    per order of the run-length kernel from the committed ncu summary, or None
+    when no summary covers this workload or the kernel's sources changed since
+    the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"fast_kernel_{workload}_counters.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"^- source sha256 \(ko_fast.cu \+ ko_fast.h\): ([0-9a-f]{64})$", text, re.M)
+    if not mh or mh.group(1) != source_hash():
+        return None
+    out = {}
+    for key in ("issue_active_pct", "threads_per_inst", "warp_inst_per_order", "case"):
+        m = re.search(rf"^- {key}: (.+)$", text, re.M)
+        if m:
+            v = m.group(1).strip()
+            try:
+                out[key] = float(v)
+            except ValueError:
+                out[key] = v
+    return out or None
+
+
+def source_hash():
     h = hashlib.sha256()
     for f in ("ko_fast.cu", "ko_fast.h"):
         with open(os.path.join(ROOT, "paper_1511_07983_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return int(mb.group(1)) if h.hexdigest() == mh.group(1) else None
+    return h.hexdigest()
 
 
 def measured_peaks():
@@ -306,7 +334,13 @@ def run_ours(a):
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gops = sm_count * 4 * 32 * max_mhz * 1e6 / 1e9   # 32-bit integer lane-ops / s
+    issue_gops = sm_count * 4 * 32 * max_mhz * 1e6 / 1e9   # every issue slot a full-warp integer op
+    # measured integer peak: add / xor / min chains on every SM (ko_hw_int_peak), clocks sampled
+    iclk = Clocks(local)
+    iclk.start()
+    int_ops, int_ms = ko.ko_hw_int_peak(16384)
+    iclk_stats = iclk.stop()
+    peak_gops = int_ops / int_ms / 1e6
     placements = placements_per_exhaustive(kset.kernels.tolist())
     kernel_s = statistics.mean(sim_ms) / 1e3
     achieved = placements * OPS_PER_PLACEMENT / kernel_s / 1e9
@@ -335,7 +369,12 @@ def run_ours(a):
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "fast_kernel", "kernel_ms": kernel_s * 1e3,
                      "placements_per_launch": placements, "ops_per_placement": OPS_PER_PLACEMENT,
-                     "peak_from": f"{sm_count} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz"},
+                     "peak_from": f"measured: ko_hw_int_peak, {int_ops} 32-bit add/xor/min lane-ops "
+                                  f"in {int_ms:.3f} ms on {sm_count} SMs",
+                     "peak_clocks": iclk_stats,
+                     "issue_peak": issue_gops,
+                     "issue_peak_from": f"{sm_count} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz",
+                     "ncu": measured_counters(a.workload)},
         "cpu_baseline": cb,
         "e2e": {"value": whole_job_rate(n_orders, a.steps, world, e2e_elapsed), "unit": "orders/s",
                 "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,
@@ -428,10 +467,76 @@ def surrogate_experiment(seed=7, train_sets=256, pairs=8192, steps=1500, batch=4
             "per_set": rows}
 
 
+BATCH_WORKLOADS = {"sets10": (64, NBINS), "batched": (4096, 0)}
+
+
+def run_batch(a):
+    """Batched workloads: the 64 ten-kernel sets on a 15-SM GPU with 4096-bin
+    histograms, or the 4096 mixed sets (N 5..10 on 13/15/148-SM GPUs) with
+    per-set min / max / rank; one step = one replay of the batch's captured
+    graph (every order of every set), timed with CUDA events."""
+    import torch
+
+    from paper_1511_07983_gb300 import build, ko, synth
+    build.build()
+    torch.cuda.set_device(0)
+    nsets, nbins = BATCH_WORKLOADS[a.workload]
+    sets = [synth.gen_set(a.workload, i) for i in range(nsets)]
+    gpus = [ko.Gpu.from_set(s) for s in sets]
+    tune = None
+    if a.lanes or a.levels is not None:
+        for g in gpus:
+            g.configure(lanes=a.lanes, levels=a.levels)
+    elif a.autotune:
+        t0 = time.perf_counter()
+        ko.ko_batch_autotune(gpus, os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"))
+        choices = sorted({(ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
+                           ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL)) for g in gpus})
+        tune = {"seconds": round(time.perf_counter() - t0, 2),
+                "choices (lanes, levels, global slab)": [list(c) for c in choices]}
+    t0 = time.perf_counter()
+    b = ko.Batch(gpus, nbins=nbins)
+    build_s = time.perf_counter() - t0
+    orders = b.orders()
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        b.run(stream=stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    launches0 = ko.ko_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        res, _ = b.run(stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    line = {"metric": "exact orders evaluated/s, batched", "value": orders * a.steps / elapsed,
+            "unit": "orders/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * elapsed / a.steps, "higher_is_better": True, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {nsets} sets, {orders} orders per step, "
+                                   f"{'4096-bin histograms' if nbins else 'per-set min/max/rank'}, "
+                                   f"one captured graph", "autotune": tune,
+                       "graph_build_s": round(build_s, 2)},
+            "gpu_launches": ko.ko_kernel_launches() - launches0, "clocks": clk,
+            "fallback_items": b.fallback_items(),
+            "heuristic_percentile_mean": sum(r["percentile"] for r in res) / len(res)}
+    print(json.dumps(line), flush=True)
+    b.close()
+    for g in gpus:
+        g.close()
+    return 0
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload in BATCH_WORKLOADS:
+        return run_batch(a)
     return run_ours(a)
 
 

@@ -192,8 +192,11 @@ ko_status ko_rank_order(ko_gpu *g, const int32_t *order, ko_rank *out, uint64_t 
 ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 
 /* Tuning knobs of the device simulators (set by the tuner; per handle).
- *   KO_OPT_LANES        lanes that share one simulation in the run-length
- *                       simulator: 16 or 32 (default 16)
+ *   KO_OPT_LANES        threads per simulation: 1 = one thread per order,
+ *                       its state in shared memory, followed by the
+ *                       run-length passes for the work items it cannot hold;
+ *                       16 or 32 = lanes sharing one run-length simulation,
+ *                       its state packed in registers (default 16)
  *   KO_OPT_LEVELS       prefix-sharing depth: exhaustive work items fix the
  *                       first N-1-levels kernels and walk the rest depth
  *                       first, saving `levels` states; 0..6 (default 4)
@@ -219,15 +222,29 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 /* Current value of a tuning knob (KO_OPT_*), or KO_ERR_ARG. */
 int64_t ko_get_option(const ko_gpu *g, int32_t key);
 
-/* Autotuner: times the run-length simulator on a calibration slice of this
- * set's exhaustive space (at least 16 work items per resident simulation and
- * about 4M orders, at most 64M) for every candidate (16 or 32 lanes per
- * simulation; 1..min(N-1, 5) saved DFS levels), keeps the fastest
- * and sets KO_OPT_LANES / KO_OPT_LEVELS on the
- * handle.  With cache_path (nullable) the choice is looked up first and
- * stored after, keyed by (N_SM class, N), in a small JSON file.  Synchronises
- * `stream`; results never depend on the choice.  N <= 12. */
+/* Autotuner: times the exhaustive simulators on a calibration slice of this
+ * set's exhaustive space (the whole space up to 64M orders, else 64M orders in
+ * 16 evenly spread ranges) for every candidate -- 1, 16 or 32 threads per
+ * simulation; for 16 and 32, saved DFS node states in a global slab or in
+ * shared memory; 1..min(N-1, 5) saved DFS levels -- keeps the fastest and sets
+ * KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL on the handle.  With
+ * cache_path (nullable) the choice is looked up first and stored after, keyed
+ * by (N_SM class, N), in a small JSON file.  Synchronises `stream`; results
+ * never depend on the choice.  N <= 12. */
 ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream);
+
+/* Autotuner for a batch of handles (call before ko_batch_create): groups the
+ * sets by (N_SM class, N); for every class with at least 2^21 orders in the
+ * batch it runs up to 64 of the class's own sets (the first ones, until 2^22
+ * orders) together as one exhaustive launch per candidate (the candidates of
+ * ko_autotune) and keeps the fastest, so small sets are timed as a batch runs
+ * them; smaller classes keep 16 lanes, a global slab and min(N-1, 4) levels.
+ * Sets every handle's KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL.  With
+ * cache_path (nullable) each class's choice is looked up first and stored
+ * after (keys "B_S<class>_N<n>").  KO_ERR_TOO_LARGE for N > 12,
+ * KO_ERR_OVERFLOW for a set whose durations reach 2^31 cycles.  Synchronises
+ * `stream`; results never depend on the choice. */
+ko_status ko_batch_autotune(ko_gpu *const *sets, int32_t nsets, const char *cache_path, void *stream);
 
 /* Work items the last exhaustive or index-list call moved from the
  * run-length simulator to its wider second pass (a simulation needed more runs
@@ -255,9 +272,10 @@ ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h);
  * Many independent sets scored in one persistent launch (the exhaustive
  * evaluation of Sec. 6 repeated over a population of kernel sets).
  *
- * ko_batch_create snapshots nsets handles (kernels, limits, capacities and
- * each handle's KO_OPT_LEVELS; KO_OPT_LANES and KO_OPT_RUN_LIMIT of the
- * first handle), computes
+ * ko_batch_create snapshots nsets handles (kernels, limits, capacities, each
+ * handle's KO_OPT_LEVELS, KO_OPT_LANES and KO_OPT_STACK_GLOBAL -- sets that
+ * share lanes and node-state placement run in one launch, one launch per
+ * such group -- and KO_OPT_RUN_LIMIT of the first handle), computes
  * each set's Algorithm 1 order on the host, lays out one work list over all
  * sets (largest sets first) and captures the whole evaluation -- reset,
  * ranked-order makespans, all N! orders of every set, optional per-set

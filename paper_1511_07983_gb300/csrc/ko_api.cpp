@@ -652,12 +652,35 @@ ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream)
     ko_status s = prepare(g, st);
     if (s) return fail(s);
     if ((s = upload_meta(g, st))) return fail(s);
-    int lanes = 16, levels = 4;
+    int lanes = 16, levels = 4, stack = 1;
     double rate = 0.0;
-    s = ko_tune_set(&g->fast, g->h, g->d_set, g->d_acc, cache_path, st, &lanes, &levels, &rate);
+    s = ko_tune_set(&g->fast, g->h, g->d_set, g->d_acc, cache_path, st, &lanes, &levels, &stack, &rate);
     if (s) return fail(s);
     g->fast.lanes = lanes;
     g->fast.levels = levels;
+    g->fast.stack_global = stack;
+    return ok();
+}
+
+ko_status ko_batch_autotune(ko_gpu *const *sets, int32_t nsets, const char *cache_path, void *stream)
+{
+    if (!sets || nsets < 1) return fail(KO_ERR_ARG);
+    std::vector<const KoSet *> hs(nsets);
+    for (int i = 0; i < nsets; i++) {
+        if (!sets[i] || sets[i]->h.n < 1) return fail(KO_ERR_ARG);
+        if (sets[i]->h.n > KO_MAX_EXHAUSTIVE) return fail(KO_ERR_TOO_LARGE);
+        if (!ko_fast_applicable(sets[i]->h)) return fail(KO_ERR_OVERFLOW);
+        hs[i] = &sets[i]->h;
+    }
+    std::vector<int> lanes(nsets), levels(nsets), stack(nsets);
+    ko_status s = ko_tune_batch(hs.data(), nsets, cache_path, (cudaStream_t)stream, lanes.data(), levels.data(),
+                                stack.data());
+    if (s) return fail(s);
+    for (int i = 0; i < nsets; i++) {
+        sets[i]->fast.lanes = lanes[i];
+        sets[i]->fast.levels = levels[i];
+        sets[i]->fast.stack_global = stack[i];
+    }
     return ok();
 }
 
@@ -680,7 +703,7 @@ ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
         return nullptr;
     }
     std::vector<const KoSet *> hs(nsets);
-    std::vector<int> levels(nsets);
+    std::vector<int> levels(nsets), lanes(nsets), stack(nsets);
     for (int i = 0; i < nsets; i++) {
         if (!sets[i] || sets[i]->h.sampling != KO_SAMPLE_BURST_END) {
             fail(KO_ERR_ARG);
@@ -689,9 +712,11 @@ ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
         sets[i]->frozen = true;
         hs[i] = &sets[i]->h;
         levels[i] = sets[i]->fast.levels;
+        lanes[i] = sets[i]->fast.lanes;
+        stack[i] = sets[i]->fast.stack_global;
     }
     ko_status err = KO_OK;
-    ko_batch *b = ko_batch_build(hs.data(), levels.data(), nsets, nbins, sets[0]->fast.lanes,
+    ko_batch *b = ko_batch_build(hs.data(), levels.data(), lanes.data(), stack.data(), nsets, nbins,
                                  sets[0]->fast.run_limit, &err);
     if (!b) fail(err);
     else ok();

@@ -5,10 +5,12 @@
 //   1. reset of every set's accumulators;
 //   2. one run-length pass evaluating each set's ranked order (Algorithm 1 by
 //      default) into a per-set reference makespan;
-//   3. one run-length pass over all sets' exhaustive work items, chunks in
-//      decreasing order of estimated cost (longest processing time first) so
-//      the largest sets start first and small sets fill the tail; abandoned
-//      items go through the wide pass and the simple simulator;
+//   3. one exhaustive launch per group of sets that share a simulator choice
+//      (threads per simulation and node-state placement, per set from its
+//      handle, usually picked per (N_SM class, N) by ko_batch_autotune): each
+//      group's work items, chunks in decreasing order of estimated cost
+//      (longest processing time first) so the largest sets start first and
+//      small sets fill the tail; abandoned items go on to the later passes;
 //   4. optionally, per-set histograms of the stored makespans;
 //   5. copies of the accumulators and references to pinned host memory.
 // No step waits on the host, so one cudaGraphLaunch runs the whole batch.
@@ -39,6 +41,13 @@ struct ko_batch {
     KoAccum *h_accs = nullptr;        // pinned
     long long *h_refs = nullptr;      // pinned
     int levels_max = 1;
+    struct Group {
+        int lanes, stack;
+        int chunk0, nchunks;      // into the exhaustive chunks
+        long long n_items;
+        int levels;               // deepest saved levels of its sets
+    };
+    std::vector<Group> groups;
     size_t slab = 0;
     KoFastState fast{};
     cudaStream_t cap_stream = nullptr;
@@ -88,18 +97,24 @@ ko_status enqueue(ko_batch *b, cudaStream_t st)
     w.perms = b->d_rows;
     w.out = (int64_t *)b->d_refs;
     w.levels = 1;
+    b->fast.lanes = 16;
+    b->fast.stack_global = 1;
     ko_status s = ko_fast_launch(&b->fast, w, b->slab, st);
     if (s) return s;
-    KoWork x{};
-    x.sets = b->d_sets;
-    x.chunks = b->d_chunks + b->n_ref_chunks;
-    x.nchunks = b->n_ex_chunks;
-    x.n_items = b->n_ex_items;
-    x.refs = b->d_refs;
-    x.accs = b->d_accs;
-    x.out = b->d_ms;
-    x.levels = b->levels_max;
-    if ((s = ko_fast_launch(&b->fast, x, b->slab, st))) return s;
+    for (const ko_batch::Group &gr : b->groups) {
+        KoWork x{};
+        x.sets = b->d_sets;
+        x.chunks = b->d_chunks + b->n_ref_chunks + gr.chunk0;
+        x.nchunks = gr.nchunks;
+        x.n_items = gr.n_items;
+        x.refs = b->d_refs;
+        x.accs = b->d_accs;
+        x.out = b->d_ms;
+        x.levels = gr.levels;
+        b->fast.lanes = gr.lanes;
+        b->fast.stack_global = gr.stack;
+        if ((s = ko_fast_launch(&b->fast, x, b->slab, st))) return s;
+    }
     if (b->nbins > 0) {
         if (cudaMemsetAsync(b->d_hist, 0, sizeof(unsigned long long) * b->nbins * b->nsets, st) !=
             cudaSuccess)
@@ -120,8 +135,8 @@ ko_status enqueue(ko_batch *b, cudaStream_t st)
 
 }  // namespace
 
-ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets, int nbins, int lanes,
-                         int run_limit, ko_status *err)
+ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int *lanes, const int *stack,
+                         int nsets, int nbins, int run_limit, ko_status *err)
 {
     *err = KO_OK;
     if (nsets < 1 || nbins < 0 || nbins > 32768) { *err = KO_ERR_ARG; return nullptr; }
@@ -129,7 +144,6 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
     if (!b) { *err = KO_ERR_NOMEM; return nullptr; }
     b->nsets = nsets;
     b->nbins = nbins;
-    b->fast.lanes = lanes;
     b->fast.run_limit = run_limit;
     b->h_sets.resize(nsets);
     std::vector<int8_t> rows((size_t)nsets * KO_MAX_KERNELS, 0);
@@ -156,10 +170,12 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
     }
     b->n_ref_chunks = nsets;
     b->n_ref_items = nsets;
-    // exhaustive chunks, most expensive set first
+    // exhaustive chunks: grouped by simulator choice, most expensive set first in each group
     std::vector<int> idx(nsets);
     std::iota(idx.begin(), idx.end(), 0);
+    auto gkey = [&](int i) { return lanes[i] * 2 + (stack[i] ? 1 : 0); };
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        if (gkey(x) != gkey(y)) return gkey(x) < gkey(y);
         return kFact[b->h_sets[x].n] * order_cost(b->h_sets[x]) > kFact[b->h_sets[y].n] * order_cost(b->h_sets[y]);
     });
     b->ms_off.assign(nsets, 0);
@@ -169,8 +185,14 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
         off += kFact[b->h_sets[i].n];
     }
     b->ms_total = off;
-    long long first = 0;
-    for (int i : idx) {
+    long long first = 0, total_items = 0;
+    for (int k = 0; k < nsets; k++) {
+        const int i = idx[k];
+        if (k == 0 || gkey(i) != gkey(idx[k - 1])) {
+            b->groups.push_back(ko_batch::Group{lanes[i], stack[i] ? 1 : 0, k, 0, 0, 1});
+            first = 0;  // each group is its own launch, items counted from 0
+        }
+        ko_batch::Group &gr = b->groups.back();
         const KoSet &h = b->h_sets[i];
         int lv = levels[i];
         int d0 = h.n - 1 - lv;
@@ -184,10 +206,14 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
         c.out_off = b->ms_off[i];
         chunks.push_back(c);
         first += c.count;
+        gr.nchunks++;
+        gr.n_items = first;
+        gr.levels = std::max(gr.levels, h.n - 1 - d0);
         b->levels_max = std::max(b->levels_max, h.n - 1 - d0);
+        total_items += c.count;
     }
     b->n_ex_chunks = nsets;
-    b->n_ex_items = first;
+    b->n_ex_items = total_items;
     bool okm = dev_alloc(&b->d_sets, nsets) && dev_alloc(&b->d_chunks, chunks.size()) &&
                dev_alloc(&b->d_rows, rows.size()) && dev_alloc(&b->d_refs, nsets) &&
                dev_alloc(&b->d_accs, nsets) && (nbins == 0 || dev_alloc(&b->d_ms, b->ms_total)) &&
@@ -209,20 +235,27 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, int nsets,
         *err = KO_ERR_CUDA;
         return nullptr;
     }
-    // allocate the run-length simulator's buffers outside capture
-    KoWork none{};
-    none.sets = b->d_sets;
-    none.chunks = b->d_chunks;
-    none.nchunks = 1;
-    none.n_items = 0;
-    none.levels = b->levels_max;  // the deepest launch of the batch sizes the node-state slab
-    none.reserve_items = std::max(b->n_ref_items, b->n_ex_items);  // and its longest one the item lists
-    if (ko_fast_launch(&b->fast, none, b->slab, b->cap_stream) != KO_OK ||
-        cudaStreamSynchronize(b->cap_stream) != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        *err = KO_ERR_CUDA;
-        return nullptr;
+    // allocate the simulators' buffers outside capture: one empty launch per
+    // group, each with its choice, its deepest levels and the longest list
+    long long longest = b->n_ref_items;
+    for (const ko_batch::Group &gr : b->groups) longest = std::max(longest, gr.n_items);
+    for (const ko_batch::Group &gr : b->groups) {
+        KoWork none{};
+        none.sets = b->d_sets;
+        none.chunks = b->d_chunks;
+        none.nchunks = 1;
+        none.n_items = 0;
+        none.levels = gr.levels;
+        none.reserve_items = longest;
+        b->fast.lanes = gr.lanes;
+        b->fast.stack_global = gr.stack;
+        if (ko_fast_launch(&b->fast, none, b->slab, b->cap_stream) != KO_OK ||
+            cudaStreamSynchronize(b->cap_stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            *err = KO_ERR_CUDA;
+            return nullptr;
+        }
     }
     // capture the whole batch once
     if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -257,7 +290,10 @@ ko_status ko_batch_exec(ko_batch *b, ko_rank *out, uint64_t *hist, bool hist_dev
         cudaGetLastError();
         return KO_ERR_CUDA;
     }
-    ko_count_launch(b->nsets * (b->nbins > 0 ? 1 : 0) + 7);
+    // reset, the reference-order passes (three), each group's passes (three, four with the one-thread pass)
+    ko_count_launch(b->nsets * (b->nbins > 0 ? 1 : 0) + 4 + 3 * (int)b->groups.size() +
+                    (int)std::count_if(b->groups.begin(), b->groups.end(),
+                                       [](const ko_batch::Group &g) { return g.lanes == 1; }));
     if (hist && b->nbins > 0) {
         const size_t bytes = sizeof(unsigned long long) * b->nbins * b->nsets;
         if (cudaMemcpyAsync(hist, b->d_hist, bytes, hist_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

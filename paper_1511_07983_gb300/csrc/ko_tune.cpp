@@ -1,10 +1,21 @@
-// Autotuner for the run-length simulator: picks the lanes per simulation
-// (16 or 32) and the prefix-sharing depth (saved DFS levels) per
-// (N_SM class, N) by timing a calibration slice of the handle's own
-// exhaustive space, and caches the choice in a small JSON file.
+// Autotuner of the exhaustive simulators: picks the threads per simulation
+// (1: one thread per order with its state in shared-memory columns; 16 or 32:
+// the run-length simulator with its state packed in registers, one run per
+// lane), where the run-length simulator keeps its saved DFS node states (a
+// global slab or shared memory), and the prefix-sharing depth (saved DFS
+// levels), per (N_SM class, N), by timing the candidates on the same orders,
+// and caches the choice in a small JSON file.
 //
-// Cache format (one object, one entry per key):
-//   {"S148_N12": {"lanes": 32, "levels": 4, "orders_per_s": 2.8e7}, ...}
+// Two tuners share the candidates and the cache:
+//   ko_tune_set    one handle: a calibration slice of its own exhaustive space;
+//   ko_tune_batch  a batch: per class, a sample of the batch's own sets of that
+//                  class run together as one launch (enough of them that the
+//                  launch fills the GPU), so small sets are timed the way a
+//                  batch runs them, not by their launch overhead.
+//
+// Cache format (one object, one entry per key; batch entries start with "B_"):
+//   {"S160_N12": {"lanes": 16, "levels": 4, "stack": 1, "orders_per_s": 8.4e7}, ...}
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -17,7 +28,7 @@
 namespace {
 
 struct Choice {
-    int lanes = 16, levels = 4;
+    int lanes = 16, levels = 4, stack = 1;
     double rate = 0.0;
 };
 
@@ -52,22 +63,24 @@ std::map<std::string, Choice> read_cache(const char *path)
         if (q1 == std::string::npos) break;
         const std::string key = text.substr(q0 + 1, q1 - q0 - 1);
         const size_t close = text.find('}', q1);
-        if (key.empty() || key[0] != 'S' || close == std::string::npos) {
+        if (key.empty() || (key[0] != 'S' && key[0] != 'B') || close == std::string::npos) {
             pos = q1 + 1;
             continue;
         }
         const std::string body = text.substr(q1, close - q1);
         Choice c;
-        int lanes = 0, levels = -1;
+        int lanes = 0, levels = -1, stack = 1;
         double rate = 0.0;
         const size_t pl = body.find("\"lanes\":"), pv = body.find("\"levels\":"),
-                     pr = body.find("\"orders_per_s\":");
+                     pr = body.find("\"orders_per_s\":"), ps = body.find("\"stack\":");
         if (pl != std::string::npos) lanes = std::atoi(body.c_str() + pl + 8);
         if (pv != std::string::npos) levels = std::atoi(body.c_str() + pv + 9);
         if (pr != std::string::npos) rate = std::atof(body.c_str() + pr + 15);
-        if ((lanes == 16 || lanes == 32) && levels >= 0 && levels <= 6) {
+        if (ps != std::string::npos) stack = std::atoi(body.c_str() + ps + 8);
+        if ((lanes == 1 || lanes == 16 || lanes == 32) && levels >= 0 && levels <= 6 && (stack == 0 || stack == 1)) {
             c.lanes = lanes;
             c.levels = levels;
+            c.stack = stack;
             c.rate = rate;
             m[key] = c;
         }
@@ -85,8 +98,8 @@ void write_cache(const char *path, const std::map<std::string, Choice> &m)
     std::fprintf(f, "{\n");
     size_t i = 0;
     for (const auto &kv : m) {
-        std::fprintf(f, "  \"%s\": {\"lanes\": %d, \"levels\": %d, \"orders_per_s\": %.6g}%s\n",
-                     kv.first.c_str(), kv.second.lanes, kv.second.levels, kv.second.rate,
+        std::fprintf(f, "  \"%s\": {\"lanes\": %d, \"levels\": %d, \"stack\": %d, \"orders_per_s\": %.6g}%s\n",
+                     kv.first.c_str(), kv.second.lanes, kv.second.levels, kv.second.stack, kv.second.rate,
                      ++i < m.size() ? "," : "");
     }
     std::fprintf(f, "}\n");
@@ -133,14 +146,58 @@ long long ko_tune_chunks(int n, int d0, std::vector<KoChunk> &out)
     return first;
 }
 
-// Times one candidate on the calibration slice; returns orders per second
-// (0 on failure).  d_set / d_chunks / d_acc are device scratch of the caller
-// (d_chunks holds kSliceChunks entries).
+// Times one launch over `w` with the candidate's lanes and node-state
+// placement (best of `reps`); returns orders per second (0 on failure).
+static double time_candidate(KoFastState *fs, const KoWork &w, KoAccum *d_acc, int nacc, long long orders,
+                             int lanes, int stack, size_t slab, int reps, cudaStream_t st)
+{
+    const int saved_lanes = fs->lanes, saved_stack = fs->stack_global;
+    fs->lanes = lanes;
+    fs->stack_global = stack;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double rate = 0.0;
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        for (int rep = 0; rep < reps; rep++) {
+            if (ko_launch_accum_reset(d_acc, nacc, st) != cudaSuccess) break;
+            cudaEventRecord(e0, st);
+            if (ko_fast_launch(fs, w, slab, st) != KO_OK) break;
+            cudaEventRecord(e1, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms > 0.0f) rate = std::max(rate, (double)orders / (ms * 1e-3));
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    fs->lanes = saved_lanes;
+    fs->stack_global = saved_stack;
+    return rate;
+}
+
+// The candidates: one thread per order (its node states always in the global
+// slab), or 16 / 32 lanes with node states in the global slab or in shared
+// memory; 1 .. min(N - 1, 5) saved levels each.
+static std::vector<Choice> candidates(int n)
+{
+    std::vector<Choice> c;
+    const int max_levels = n - 1 < 5 ? n - 1 : 5;
+    for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
+        c.push_back(Choice{1, levels, 1, 0.0});
+        for (int lanes : {16, 32})
+            for (int stack : {1, 0}) c.push_back(Choice{lanes, levels, stack, 0.0});
+    }
+    return c;
+}
+
+// Times one candidate on the calibration slice of one set.  d_set / d_chunks /
+// d_acc are device scratch of the caller (d_chunks holds kSliceChunks entries).
 double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoChunk *d_chunks,
-                       KoAccum *d_acc, int lanes, int levels, int reps, cudaStream_t st)
+                       KoAccum *d_acc, const Choice &cand, int reps, cudaStream_t st)
 {
     const int n = h.n;
-    int d0 = n - 1 - levels;
+    int d0 = n - 1 - cand.levels;
     if (d0 < 0) d0 = 0;
     const long long span = kFact[n - d0];
     if (span > kSpanAll) return 0.0;
@@ -157,37 +214,13 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
     w.n_items = items;
     w.accs = d_acc;
     w.levels = n - 1 - d0 > 0 ? n - 1 - d0 : 1;
-    const int saved_lanes = fs->lanes;
-    fs->lanes = lanes;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        cudaGetLastError();
-        if (e0) cudaEventDestroy(e0);
-        fs->lanes = saved_lanes;
-        return 0.0;
-    }
-    double rate = 0.0;
-    for (int rep = 0; rep < reps; rep++) {
-        if (ko_launch_accum_reset(d_acc, 1, st) != cudaSuccess) break;
-        cudaEventRecord(e0, st);
-        if (ko_fast_launch(fs, w, ko_slab_bytes(h.S, h.Bk), st) != KO_OK) break;
-        cudaEventRecord(e1, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms > 0.0f) rate = (double)(items * span) / (ms * 1e-3);
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaGetLastError();
-    fs->lanes = saved_lanes;
-    return rate;
+    return time_candidate(fs, w, d_acc, 1, items * span, cand.lanes, cand.stack, ko_slab_bytes(h.S, h.Bk), reps, st);
 }
 
-// Pick lanes/levels for the handle's set; returns KO_OK and the choice.
+// Pick lanes / levels / node-state placement for the handle's set.
 ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAccum *d_acc,
                       const char *cache_path, cudaStream_t st, int *lanes_out, int *levels_out,
-                      double *rate_out)
+                      int *stack_out, double *rate_out)
 {
     const std::string key = key_of(h);
     std::map<std::string, Choice> cache = read_cache(cache_path);
@@ -195,27 +228,24 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAcc
     if (it != cache.end()) {
         *lanes_out = it->second.lanes;
         *levels_out = it->second.levels;
+        *stack_out = it->second.stack;
         *rate_out = it->second.rate;
         return KO_OK;
     }
     Choice best;
     best.rate = -1.0;
-    const int max_levels = h.n - 1 < 5 ? h.n - 1 : 5;
     KoChunk *d_chunks = nullptr;
     if (cudaMalloc((void **)&d_chunks, sizeof(KoChunk) * kSliceChunks) != cudaSuccess) {
         cudaGetLastError();
         return KO_ERR_NOMEM;
     }
     bool warmed = false;
-    for (int lanes : {32, 16}) {
-        for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
-            const double r = ko_tune_measure(fs, h, d_set, d_chunks, d_acc, lanes, levels, warmed ? 1 : 2, st);
-            warmed = true;
-            if (r > best.rate) {
-                best.rate = r;
-                best.lanes = lanes;
-                best.levels = levels;
-            }
+    for (const Choice &c : candidates(h.n)) {
+        const double r = ko_tune_measure(fs, h, d_set, d_chunks, d_acc, c, warmed ? 1 : 2, st);
+        warmed = true;
+        if (r > best.rate) {
+            best = c;
+            best.rate = r;
         }
     }
     cudaFree(d_chunks);
@@ -224,6 +254,112 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAcc
     write_cache(cache_path, cache);
     *lanes_out = best.lanes;
     *levels_out = best.levels;
+    *stack_out = best.stack;
     *rate_out = best.rate;
     return KO_OK;
+}
+
+// Per-class choices for a batch.  For every (N_SM class, N) class of the
+// batch with at least kBatchMinOrders orders, up to kBatchSample of its sets
+// (the first ones, until kBatchOrders orders) run together as one exhaustive
+// launch per candidate; classes below that size keep the default.
+constexpr long long kBatchMinOrders = 1ll << 21;
+constexpr long long kBatchOrders = 1ll << 22;
+constexpr int kBatchSample = 64;
+
+ko_status ko_tune_batch(const KoSet *const *hs, int nsets, const char *cache_path, cudaStream_t st,
+                        int *lanes_out, int *levels_out, int *stack_out)
+{
+    std::map<std::string, std::vector<int>> classes;
+    for (int i = 0; i < nsets; i++) classes["B_" + key_of(*hs[i])].push_back(i);
+    std::map<std::string, Choice> cache = read_cache(cache_path);
+    bool dirty = false;
+    KoSet *d_sets = nullptr;
+    KoChunk *d_chunks = nullptr;
+    KoAccum *d_accs = nullptr;
+    if (cudaMalloc((void **)&d_sets, sizeof(KoSet) * kBatchSample) != cudaSuccess ||
+        cudaMalloc((void **)&d_chunks, sizeof(KoChunk) * kBatchSample) != cudaSuccess ||
+        cudaMalloc((void **)&d_accs, sizeof(KoAccum) * kBatchSample) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_sets); cudaFree(d_chunks); cudaFree(d_accs);
+        return KO_ERR_NOMEM;
+    }
+    ko_status status = KO_OK;
+    KoFastState fs{};
+    for (const auto &kv : classes) {
+        const std::vector<int> &members = kv.second;
+        const KoSet &h0 = *hs[members[0]];
+        Choice choice;
+        choice.levels = h0.n - 1 < 4 ? h0.n - 1 : 4;
+        auto it = cache.find(kv.first);
+        const long long class_orders = (long long)members.size() * kFact[h0.n];
+        if (it != cache.end()) {
+            choice = it->second;
+        } else if (class_orders >= kBatchMinOrders) {
+            std::vector<KoSet> sample;
+            long long orders = 0;
+            for (int i : members) {
+                if ((int)sample.size() >= kBatchSample || orders >= kBatchOrders) break;
+                sample.push_back(*hs[i]);
+                orders += kFact[hs[i]->n];
+            }
+            size_t slab = 0;
+            for (const KoSet &x : sample) slab = std::max(slab, ko_slab_bytes(x.S, x.Bk));
+            if (cudaMemcpyAsync(d_sets, sample.data(), sizeof(KoSet) * sample.size(), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess) {
+                status = KO_ERR_CUDA;
+                break;
+            }
+            Choice best;
+            best.rate = -1.0;
+            bool warmed = false;
+            for (const Choice &c : candidates(h0.n)) {
+                std::vector<KoChunk> chunks;
+                long long first = 0;
+                const int d0 = std::max(0, h0.n - 1 - c.levels);
+                for (int j = 0; j < (int)sample.size(); j++) {
+                    KoChunk ch{};
+                    ch.first = first;
+                    ch.count = kFact[sample[j].n] / kFact[sample[j].n - d0];
+                    ch.set = j;
+                    ch.d0 = d0;
+                    chunks.push_back(ch);
+                    first += ch.count;
+                }
+                if (cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(KoChunk) * chunks.size(),
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    break;
+                KoWork w{};
+                w.sets = d_sets;
+                w.chunks = d_chunks;
+                w.nchunks = (int)chunks.size();
+                w.n_items = first;
+                w.accs = d_accs;
+                w.levels = std::max(1, h0.n - 1 - d0);
+                const double r = time_candidate(&fs, w, d_accs, (int)sample.size(), orders, c.lanes, c.stack,
+                                                slab, warmed ? 1 : 2, st);
+                warmed = true;
+                if (r > best.rate) {
+                    best = c;
+                    best.rate = r;
+                }
+            }
+            if (best.rate <= 0.0) {
+                status = KO_ERR_CUDA;
+                break;
+            }
+            choice = best;
+            cache[kv.first] = best;
+            dirty = true;
+        }
+        for (int i : members) {
+            lanes_out[i] = choice.lanes;
+            levels_out[i] = choice.levels;
+            stack_out[i] = choice.stack;
+        }
+    }
+    ko_fast_release(&fs);
+    cudaFree(d_sets); cudaFree(d_chunks); cudaFree(d_accs);
+    if (status == KO_OK && dirty) write_cache(cache_path, cache);
+    return status;
 }

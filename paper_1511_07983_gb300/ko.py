@@ -98,6 +98,7 @@ _SIGNATURES = {
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "ko_batch_autotune": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_void_p]),
     "ko_hw_create": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
     "ko_hw_regs": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "ko_hw_int_peak": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -405,6 +406,14 @@ def ko_batch_fallback_items(b):
 
 def ko_batch_destroy(b):
     lib().ko_batch_destroy(b)
+
+
+def ko_batch_autotune(gpus, cache_path=None, stream=None):
+    """Per-(N_SM class, N) simulator choice for a batch of handles; sets each
+    handle's lanes / levels / node-state placement."""
+    arr = (ctypes.c_void_p * len(gpus))(*[g.h for g in gpus])
+    path = cache_path.encode() if cache_path else None
+    _check(lib().ko_batch_autotune(arr, len(gpus), path, _stream(stream)), "ko_batch_autotune")
 
 
 class Batch:
@@ -727,7 +736,8 @@ class Gpu:
     def autotune(self, cache_path=None, stream=None):
         ko_autotune(self.h, cache_path, stream)
         return {"lanes": ko_get_option(self.h, KO_OPT_LANES),
-                "levels": ko_get_option(self.h, KO_OPT_LEVELS)}
+                "levels": ko_get_option(self.h, KO_OPT_LEVELS),
+                "stack_global": ko_get_option(self.h, KO_OPT_STACK_GLOBAL)}
 
     def last_sim_ms(self):
         return ko_last_sim_ms(self.h)

@@ -114,3 +114,51 @@ def test_mixed_batch_first_512_sets(ko):
     b = ko.Batch([ko.Gpu.from_set(s) for s in sets], nbins=0)
     res, _ = b.run()
     _check_full_batch(ko, sets, res, None, 0, cross=(1, 200, 511))
+
+
+def _class_key(s):
+    S = s.gpu[0]
+    c = 16 if S <= 16 else 32 if S <= 32 else 64 if S <= 64 else 128 if S <= 128 else 160 if S <= 160 else 1024
+    return f"B_S{c}_N{s.n}"
+
+
+def test_batch_autotune_per_class(ko, tmp_path):
+    """ko_batch_autotune gives every set its class's choice, stores the timed
+    classes in the cache, and the tuned batch (one launch per choice) returns
+    what the default batch returns; small sets also match the oracle."""
+    import json
+    sets = [synth.gen_set("batched", i) for i in range(400)]
+    gpus = [ko.Gpu.from_set(s) for s in sets]
+    cache = str(tmp_path / "tune.json")
+    ko.ko_batch_autotune(gpus, cache)
+    data = json.load(open(cache))
+    by_class = {}
+    for s, g in zip(sets, gpus):
+        c = (ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
+             ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL))
+        assert c[0] in (1, 16, 32) and 1 <= c[1] <= min(s.n - 1, 5) and c[2] in (0, 1)
+        by_class.setdefault(_class_key(s), set()).add(c)
+    assert all(len(v) == 1 for v in by_class.values())
+    timed = {k for k in by_class if sum(math.factorial(s.n) for s in sets if _class_key(s) == k) >= 1 << 21}
+    assert timed and timed <= set(data)
+    for k in timed:
+        assert (data[k]["lanes"], data[k]["levels"], data[k]["stack"]) == next(iter(by_class[k]))
+    b = ko.Batch(gpus, nbins=0)
+    res, _ = b.run()
+    plain = [ko.Gpu.from_set(s) for s in sets]
+    b2 = ko.Batch(plain, nbins=0)
+    res2, _ = b2.run()
+    for r, r2 in zip(res, res2):
+        for k in ("min", "max", "makespan", "n_better", "n_equal", "n_worse", "n_total"):
+            assert r[k] == r2[k]
+    for s, r in zip(sets, res):
+        if s.n <= 6:
+            st = _oracle_stats(s, 0)
+            assert (r["min"], r["max"], r["n_better"], r["n_equal"], r["n_worse"]) == \
+                (st["min"], st["max"], st["n_better"], st["n_equal"], st["n_worse"])
+    # a second tuner call is served from the cache
+    again = [ko.Gpu.from_set(s) for s in sets[:50]]
+    ko.ko_batch_autotune(again, cache)
+    for s, g in zip(sets[:50], again):
+        assert (ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
+                ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL)) == next(iter(by_class[_class_key(s)]))
