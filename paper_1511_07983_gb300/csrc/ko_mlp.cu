@@ -225,12 +225,16 @@ __global__ void out_fwd_kernel(const uint16_t *__restrict__ a3, const uint16_t *
     if (lane == 0) y[warp] = s + b4[0];
 }
 
-// Output layer backward: dy = 2 (y - t) / B; loss sum; dw4 += dy * A3; db4 += dy;
+// Output layer backward: dy = 2 (y - t) / B; loss sum; dw4 = sum dy * A3; db4 = sum dy;
 // dZ3 = dy * w4 * [A3 > 0] (fp32 for the bias gradient, bf16 + transposed for GEMMs).
+// Each block writes its partial sums (rows r0 .. r0+31) to part[blockIdx.x]:
+// dw4 partials, db3 partials, loss, db4; part_sum_kernel adds them up in
+// block order, so the gradients do not depend on the order blocks finish in.
+constexpr int kPartOut = 2 * kHidden + 2;
+
 __global__ void out_bwd_kernel(const float *__restrict__ y, const float *__restrict__ t,
                                const uint16_t *__restrict__ a3, const uint16_t *__restrict__ w4, int B,
-                               float *loss_sum, float *dw4, float *db4, float *db3, uint16_t *dz,
-                               uint16_t *dzt)
+                               float *part, uint16_t *dz, uint16_t *dzt)
 {
     __shared__ float s_dw[kHidden], s_db[kHidden];
     for (int k = threadIdx.x; k < kHidden; k += blockDim.x) { s_dw[k] = 0.0f; s_db[k] = 0.0f; }
@@ -253,20 +257,21 @@ __global__ void out_bwd_kernel(const float *__restrict__ y, const float *__restr
         }
     }
     __syncthreads();
+    float *mine = part + (size_t)blockIdx.x * kPartOut;
     for (int k = threadIdx.x; k < kHidden; k += blockDim.x) {
-        atomicAdd(&dw4[k], s_dw[k]);
-        atomicAdd(&db3[k], s_db[k]);
+        mine[k] = s_dw[k];
+        mine[kHidden + k] = s_db[k];
     }
     if (threadIdx.x == 0) {
-        atomicAdd(loss_sum, lsum);
-        atomicAdd(db4, dbsum);
+        mine[2 * kHidden] = lsum;
+        mine[2 * kHidden + 1] = dbsum;
     }
 }
 
-// Hidden-layer ReLU backward: dZ = dA * [A > 0]; bias gradient (fp32 sums);
-// dZ as bf16 row-major and transposed.
+// Hidden-layer ReLU backward: dZ = dA * [A > 0]; bias-gradient partials per
+// block (fp32) into part[blockIdx.x]; dZ as bf16 row-major and transposed.
 __global__ void relu_bwd_kernel(const float *__restrict__ da, const uint16_t *__restrict__ a, int B,
-                                float *db, uint16_t *dz, uint16_t *dzt)
+                                float *part, uint16_t *dz, uint16_t *dzt)
 {
     __shared__ float s_db[kHidden];
     for (int k = threadIdx.x; k < kHidden; k += blockDim.x) s_db[k] = 0.0f;
@@ -284,7 +289,26 @@ __global__ void relu_bwd_kernel(const float *__restrict__ da, const uint16_t *__
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kHidden; k += blockDim.x) atomicAdd(&db[k], s_db[k]);
+    for (int k = threadIdx.x; k < kHidden; k += blockDim.x) part[(size_t)blockIdx.x * kHidden + k] = s_db[k];
+}
+
+// Column sums of nblk rows of `width` partials, rows added in order.  Columns
+// [0, span) go to lo[c], [span, 2 span) to hi[c - span], column 2 span to *s0
+// and 2 span + 1 to *s1.
+struct PartDst {
+    float *lo, *hi, *s0, *s1;
+    int span;
+};
+__global__ void part_sum_kernel(const float *__restrict__ part, int nblk, int width, PartDst dst)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= width) return;
+    float acc = 0.0f;
+    for (int b = 0; b < nblk; b++) acc += part[(size_t)b * width + c];
+    if (c < dst.span) dst.lo[c] = acc;
+    else if (c < 2 * dst.span) dst.hi[c - dst.span] = acc;
+    else if (c == 2 * dst.span) *dst.s0 = acc;
+    else *dst.s1 = acc;
 }
 
 // Adam on the FP32 master weights, then refresh the BF16 copies the GEMMs read.
@@ -507,20 +531,29 @@ cudaError_t ko_mlp_out_fwd(const uint16_t *a3, const uint16_t *w4, const float *
     return cudaGetLastError();
 }
 
+size_t ko_mlp_part_floats(int B) { return (size_t)((B + 31) / 32) * kPartOut; }
+
 cudaError_t ko_mlp_out_bwd(const float *y, const float *t, const uint16_t *a3, const uint16_t *w4, int B,
                            float *loss_sum, float *dw4, float *db4, float *db3, uint16_t *dz,
-                           uint16_t *dzt, cudaStream_t st)
+                           uint16_t *dzt, float *part, cudaStream_t st)
 {
-    out_bwd_kernel<<<(B + 31) / 32, 256, 0, st>>>(y, t, a3, w4, B, loss_sum, dw4, db4, db3, dz, dzt);
-    ko_count_launch();
+    const int nblk = (B + 31) / 32;
+    out_bwd_kernel<<<nblk, 256, 0, st>>>(y, t, a3, w4, B, part, dz, dzt);
+    // columns: dw4 [0, 256), db3 [256, 512), loss 512, db4 513
+    PartDst d{dw4, db3, loss_sum, db4, kHidden};
+    part_sum_kernel<<<(2 * kHidden + 2 + 255) / 256, 256, 0, st>>>(part, nblk, kPartOut, d);
+    ko_count_launch(2);
     return cudaGetLastError();
 }
 
 cudaError_t ko_mlp_relu_bwd(const float *da, const uint16_t *a, int B, float *db, uint16_t *dz,
-                            uint16_t *dzt, cudaStream_t st)
+                            uint16_t *dzt, float *part, cudaStream_t st)
 {
-    relu_bwd_kernel<<<(B + 31) / 32, 256, 0, st>>>(da, a, B, db, dz, dzt);
-    ko_count_launch();
+    const int nblk = (B + 31) / 32;
+    relu_bwd_kernel<<<nblk, 256, 0, st>>>(da, a, B, part, dz, dzt);
+    PartDst d{db, nullptr, nullptr, nullptr, kHidden};
+    part_sum_kernel<<<(kHidden + 255) / 256, 256, 0, st>>>(part, nblk, kHidden, d);
+    ko_count_launch(2);
     return cudaGetLastError();
 }
 

@@ -56,11 +56,14 @@ cudaError_t ko_mlp_encode(const int8_t *rows, int row_stride, const int *sid, co
                           uint16_t *xt, cudaStream_t st);
 cudaError_t ko_mlp_out_fwd(const uint16_t *a3, const uint16_t *w4, const float *b4, int B, float *y,
                            cudaStream_t st);
+// The backward kernels sum per-block partials (workspace `part`, at least
+// ko_mlp_part_floats(B) floats) in a fixed order: gradients are reproducible.
+size_t ko_mlp_part_floats(int B);
 cudaError_t ko_mlp_out_bwd(const float *y, const float *t, const uint16_t *a3, const uint16_t *w4, int B,
                            float *loss_sum, float *dw4, float *db4, float *db3, uint16_t *dz,
-                           uint16_t *dzt, cudaStream_t st);
+                           uint16_t *dzt, float *part, cudaStream_t st);
 cudaError_t ko_mlp_relu_bwd(const float *da, const uint16_t *a, int B, float *db, uint16_t *dz,
-                            uint16_t *dzt, cudaStream_t st);
+                            uint16_t *dzt, float *part, cudaStream_t st);
 cudaError_t ko_mlp_adam(float *p, float *m, float *v, const float *g, long long count, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st);
 cudaError_t ko_mlp_weights_bf16(const float *w, int K, int N, uint16_t *wk, uint16_t *wt, cudaStream_t st);

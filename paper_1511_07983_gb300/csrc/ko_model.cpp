@@ -76,6 +76,7 @@ struct ko_model {
     uint16_t *a0 = nullptr, *a0t = nullptr, *a1 = nullptr, *a1t = nullptr, *a2 = nullptr, *a2t = nullptr,
              *a3 = nullptr, *dz = nullptr, *dzt = nullptr;
     float *y = nullptr, *t = nullptr, *da = nullptr, *loss = nullptr;
+    float *part = nullptr;     // per-block bias-gradient partials (summed in a fixed order)
     int *pick = nullptr;
     KoFastState fast{};
     int tc_forward = 1;        // inference layers on tcgen05 (1) or mma.sync (0)
@@ -88,9 +89,9 @@ struct ko_model {
     void free_acts()
     {
         cudaFree(a0); cudaFree(a0t); cudaFree(a1); cudaFree(a1t); cudaFree(a2); cudaFree(a2t); cudaFree(a3);
-        cudaFree(dz); cudaFree(dzt); cudaFree(y); cudaFree(t); cudaFree(da); cudaFree(pick);
+        cudaFree(dz); cudaFree(dzt); cudaFree(y); cudaFree(t); cudaFree(da); cudaFree(pick); cudaFree(part);
         a0 = a0t = a1 = a1t = a2 = a2t = a3 = dz = dzt = nullptr;
-        y = t = da = nullptr;
+        y = t = da = part = nullptr;
         pick = nullptr;
         cap = 0;
     }
@@ -113,7 +114,7 @@ ko_status ensure_acts(ko_model *md, int B)
     bool ok = dalloc(&md->a0, in) && dalloc(&md->a0t, in) && dalloc(&md->a1, hid) && dalloc(&md->a1t, hid) &&
               dalloc(&md->a2, hid) && dalloc(&md->a2t, hid) && dalloc(&md->a3, hid) && dalloc(&md->dz, hid) &&
               dalloc(&md->dzt, hid) && dalloc(&md->y, (size_t)B) && dalloc(&md->t, (size_t)B) &&
-              dalloc(&md->da, hid) && dalloc(&md->pick, (size_t)B);
+              dalloc(&md->da, hid) && dalloc(&md->pick, (size_t)B) && dalloc(&md->part, ko_mlp_part_floats(B));
     if (!ok) {
         md->free_acts();
         return KO_ERR_NOMEM;
@@ -228,15 +229,15 @@ ko_status backward(ko_model *md, int B, float *loss_dev, cudaStream_t st)
     ko_status s;
     if (cudaMemsetAsync(md->g, 0, sizeof(float) * kParams, st) != cudaSuccess) return KO_ERR_CUDA;
     if ((s = cuda_ok(ko_mlp_out_bwd(md->y, md->t, md->a3, md->w4b, B, loss_dev, md->g + kOffW4, md->g + kOffB4,
-                                    md->g + kOffB3, md->dz, md->dzt, st))))
+                                    md->g + kOffB3, md->dz, md->dzt, md->part, st))))
         return s;
     if (md->tc_train) {
         if ((s = wgrad(md, md->a2t, kHidden, B, md->g + kOffW3, st))) return s;
         if ((s = dgrad(md, md->w3, B, st))) return s;
-        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a2, B, md->g + kOffB2, md->dz, md->dzt, st)))) return s;
+        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a2, B, md->g + kOffB2, md->dz, md->dzt, md->part, st)))) return s;
         if ((s = wgrad(md, md->a1t, kHidden, B, md->g + kOffW2, st))) return s;
         if ((s = dgrad(md, md->w2, B, st))) return s;
-        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a1, B, md->g + kOffB1, md->dz, md->dzt, st)))) return s;
+        if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a1, B, md->g + kOffB1, md->dz, md->dzt, md->part, st)))) return s;
         return wgrad(md, md->a0t, kMlpIn, B, md->g + kOffW1, st);
     }
     // layer 3
@@ -244,13 +245,13 @@ ko_status backward(ko_model *md, int B, float *loss_dev, cudaStream_t st)
         return s;
     if ((s = cuda_ok(ko_mlp_gemm_f32(md->dz, kHidden, md->w3, kHidden, B, kHidden, kHidden, md->da, kHidden, st))))
         return s;
-    if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a2, B, md->g + kOffB2, md->dz, md->dzt, st)))) return s;
+    if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a2, B, md->g + kOffB2, md->dz, md->dzt, md->part, st)))) return s;
     // layer 2
     if ((s = cuda_ok(ko_mlp_gemm_f32(md->a1t, B, md->dzt, B, kHidden, kHidden, B, md->g + kOffW2, kHidden, st))))
         return s;
     if ((s = cuda_ok(ko_mlp_gemm_f32(md->dz, kHidden, md->w2, kHidden, B, kHidden, kHidden, md->da, kHidden, st))))
         return s;
-    if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a1, B, md->g + kOffB1, md->dz, md->dzt, st)))) return s;
+    if ((s = cuda_ok(ko_mlp_relu_bwd(md->da, md->a1, B, md->g + kOffB1, md->dz, md->dzt, md->part, st)))) return s;
     // layer 1 (no input gradient needed)
     return cuda_ok(ko_mlp_gemm_f32(md->a0t, B, md->dzt, B, kMlpIn, kHidden, B, md->g + kOffW1, kHidden, st));
 }
