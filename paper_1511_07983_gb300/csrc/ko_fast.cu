@@ -710,7 +710,9 @@ fast_kernel(KoWork a)
             } else {
                 d0 = ch.d0;
                 unsigned long long j = (unsigned long long)(ch.list_off + local);
-                if (kPerWarp == 2 && d0 >= 2) {
+                // swap partners pair up only in a pass over whole chunks; an item taken from a
+                // list of abandoned items is run as the item it names
+                if (kPerWarp == 2 && d0 >= 2 && !a.item_list) {
                     j = pair_swap_order(j, n - d0 + 2, (unsigned long long)ch.list_off,
                                         (unsigned long long)(ch.list_off + ch.count));
                     rec = (unsigned long long)ch.first + (j - (unsigned long long)ch.list_off);

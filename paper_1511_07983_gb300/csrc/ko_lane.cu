@@ -23,10 +23,14 @@ namespace {
 using namespace kolane;
 
 constexpr unsigned kAll = 0xffffffffu;
-constexpr int kLaneThreads = 256;   // one block per SM: 256 columns of kWords words
+#ifndef KO_LANE_THREADS
+#define KO_LANE_THREADS 288
+#endif
+constexpr int kLaneThreads = KO_LANE_THREADS;   // one block per SM: this many columns of kWords words
+static_assert(kLaneThreads % 32 == 0 && kLaneThreads * kWords * 4 <= 232448, "one block's columns fit an SM");
 // Threads of a warp that must wait for the control step before it runs.
 #ifndef KO_LANE_GATHER
-#define KO_LANE_GATHER 8
+#define KO_LANE_GATHER 16
 #endif
 constexpr int kGather = KO_LANE_GATHER;
 
@@ -71,7 +75,7 @@ __device__ __forceinline__ int nth_unused(uint32_t used, uint32_t all, unsigned 
     return __ffs((int)u) - 1;
 }
 
-enum Phase : int { PH_FETCH = 0, PH_NEXT, PH_EVENT, PH_FINAL, PH_PLACED, PH_DONE };
+enum Phase : int { PH_FETCH = 0, PH_NEXT, PH_START, PH_EVENT, PH_FINAL, PH_PLACED, PH_DONE };
 
 template <int T>
 __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
         const bool control = __popc(want) >= kGather || busy == 0u;
         if (!control) {
             if (phase == PH_EVENT) {
-                const bool last = sim.event(left);
+                const bool last = sim.event(left, busy);
                 if (!sim.fail && ++events > total_blocks + 64) sim.fail = 1;  // each event frees >= 1 block
                 if (sim.fail) {
                     const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
@@ -119,6 +123,10 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                 }
             }
         } else {
+            // The control sub-steps run one after another, each ending at a
+            // reconvergence point: threads that took different sub-steps do
+            // not stay split for the rest of the iteration.
+            int cand = -1;
             if (phase == PH_FINAL) {  // the head kernel's last burst, deferred from its event
                 sim.place_partial(left);
                 if (sim.fail) {
@@ -129,6 +137,7 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     phase = PH_PLACED;
                 }
             }
+            __syncwarp();
             if (phase == PH_PLACED) {
                 depth++;
                 if (depth == n) {
@@ -140,7 +149,6 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     mx = u > mx ? u : mx;
                     nb += ms < ref; ne += ms == ref; nw += ms > ref;
                     // back up to the deepest node with an untried child
-                    int cand = -1;
                     while (depth > d0) {
                         depth--;
                         const int old = (int)((perm >> (4 * depth)) & 15u);
@@ -179,13 +187,7 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     } else {
                         perm = (perm & ~(15ull << (4 * depth))) | ((unsigned long long)cand << (4 * depth));
                         used |= 1u << cand;
-                        left = sim.start_kernel(cand);
-                        events = 0;
-                        phase = sim.fail ? PH_FETCH : (left > 0 ? PH_EVENT : PH_PLACED);
-                        if (sim.fail) {
-                            const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
-                            if (slot < a.ov_cap) a.ov_list[slot] = rec;
-                        }
+                        phase = PH_START;
                     }
                 } else {
                     if (depth >= d0 && n - depth >= 2) {
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     phase = PH_NEXT;
                 }
             }
+            __syncwarp();
             if (phase == PH_FETCH) {
                 for (;;) {  // until an item starts or the list is exhausted
                     const unsigned long long base = atomicAdd(a.counter, 1ull);
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     break;
                 }
             }
+            __syncwarp();
             if (phase == PH_NEXT) {
-                int cand;
                 if (depth < d0) {
                     if (mode == 2) {
                         cand = row[depth];
@@ -281,7 +284,14 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                     perm = (perm & ~(15ull << (4 * depth))) | ((unsigned long long)cand << (4 * depth));
                 }
                 used |= 1u << cand;
+                phase = PH_START;
+            }
+            __syncwarp();
+            if (phase == PH_START) {  // one call site for every kernel start
                 left = sim.start_kernel(cand);
+                // blocks still queued: the start burst has ended, so its durations are fixed
+                // here, together, rather than by the first event of each thread
+                if (left > 0) sim.close_burst();
                 events = 0;
                 if (sim.fail) {
                     const unsigned long long slot = atomicAdd(a.ov_count, 1ull);
@@ -320,10 +330,11 @@ cudaError_t ko_launch_lane(const KoWork &a, cudaStream_t st)
     long long blocks = sms;
     const long long fit = a.gstack_words / ((long long)kLaneThreads * levels * kSaveWords);
     if (blocks > fit) blocks = fit;
+    if (blocks < 1) return cudaErrorInvalidValue;  // the slab holds no thread's node states
     const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
     const long long needed = (work + kLaneThreads - 1) / kLaneThreads;
     if (blocks > needed) blocks = needed;
-    if (blocks < 1) return cudaErrorInvalidValue;
+    if (blocks < 1) blocks = 1;  // an empty list (a sizing launch): one block finds no work
     lane_kernel<kLaneThreads><<<(unsigned)blocks, kLaneThreads, smem, st>>>(a);
     ko_count_launch();
     return cudaGetLastError();

@@ -18,7 +18,9 @@
 // those runs (every other run was full for it when the last burst ended).
 // Measured on the N=12 / 148-SM set: about 11 runs and 34 groups live, 1.3 runs
 // released and 1.3 groups started per event, a split every 15 events; the last
-// burst of an order can split up to 13 runs.
+// burst of an order can split up to 13 runs.  56 slots hold every group of
+// about 99 % of the 120-order work items; the rest move on to the run-length
+// passes.
 //
 // Layout.  The state of one simulation is a column of kWords 32-bit words in
 // shared memory, word f of the thread's column at col[f * STRIDE]; with STRIDE
@@ -38,10 +40,25 @@
 #define KO_HD __host__ __device__ __forceinline__
 #endif
 
+// Reconvergence point of the threads in `mask` (device only).
+#ifdef __CUDA_ARCH__
+#define KO_RECONVERGE(mask) __syncwarp(mask)
+#else
+#define KO_RECONVERGE(mask) ((void)(mask))
+#endif
+
 namespace kolane {
 
-constexpr int kRuns = 14;   // runs one simulation may hold
-constexpr int kPool = 64;   // group slots of one simulation
+#ifndef KO_LANE_RUNS
+#define KO_LANE_RUNS 14
+#endif
+#ifndef KO_LANE_POOL
+#define KO_LANE_POOL 56
+#endif
+constexpr int kRuns = KO_LANE_RUNS;   // runs one simulation may hold (at most 16)
+constexpr int kPool = KO_LANE_POOL;   // group slots of one simulation (even, at most 64)
+static_assert(kRuns <= 16 && kPool <= 64 && kPool % 2 == 0, "run and slot masks are 32 and 64 bits");
+constexpr unsigned long long kPoolAll = kPool == 64 ? ~0ull : ((1ull << kPool) - 1ull);
 
 enum : int {
     W_RB = 0,                      // run: first SM | SM count << 16
@@ -54,7 +71,7 @@ enum : int {
     W_RG1 = W_RG0 + kRuns,         // run: pool slots 32..63
     W_GE = W_RG1 + kRuns,          // slot: end (mod 2^32)
     W_GD = W_GE + kPool,           // slots 2w, 2w+1: 16-bit descriptors
-    kWords = W_GD + kPool / 2      // 208
+    kWords = W_GD + kPool / 2      // 200 with 14 runs and 56 slots
 };
 // Descriptor: kernel (bits 0-4) | blocks per SM - 1 (bits 5-10) | owner run (bits 11-14).
 constexpr uint32_t kDescKernel = 31u, kDescOwnerShift = 11;
@@ -63,7 +80,8 @@ constexpr uint32_t kRegMask = (1u << 19) - 1u;
 
 // Registers saved with a node state (beside the kWords column words).
 constexpr int kRegWords = 12;
-constexpr int kSaveWords = kWords + kRegWords;   // 220 = 55 x 16 bytes
+constexpr int kSaveWords = kWords + kRegWords;   // 212 = 53 x 16 bytes with 14 runs and 56 slots
+static_assert(kWords % 4 == 0, "node states are copied in 16-byte pieces");
 
 // The set's limits, per thread.
 struct Limits {
@@ -187,7 +205,7 @@ struct LaneSim {
         t = 0;
         tmx = 0;
         p = 0;
-        freeg = ~0ull;
+        freeg = kPoolAll;
         pend = 0;
         rv = 0;
         fail = 0;
@@ -530,14 +548,17 @@ struct LaneSim {
     // burst, advance to the next end, release, and place the head kernel where
     // every offered SM takes its full capacity.  Returns true when the offered
     // room exceeds the queue instead; the caller then finishes the burst with
-    // place_partial (the kernel's last burst).
-    KO_HD bool event(int &left)
+    // place_partial (the kernel's last burst).  `mask`: the threads of the warp
+    // that run this event step together; they reconverge after each stage.
+    KO_HD bool event(int &left, unsigned mask)
     {
         close_burst();
+        KO_RECONVERGE(mask);
         const uint32_t fresh = advance();
-        if (fail) return false;
-        offer(fresh);
-        if (ctotal == 0) return false;
+        KO_RECONVERGE(mask);
+        offer(fail ? 0u : fresh);  // a failed simulation still reaches every reconvergence point
+        KO_RECONVERGE(mask);
+        if (fail || ctotal == 0) return false;
         if (ctotal <= left) {
             place_full(left);
             return false;

@@ -109,8 +109,9 @@ def test_single12_subspace_by_prefix(ko):
         g.eval_all(out)
         torch.cuda.synchronize()
         # a few items need more runs or group slots than one simulation holds
-        # and are finished by the run-length passes
-        assert g.last_fallback_items() < n_all // math.factorial(6) // 1000
+        # and are finished by the run-length passes (about 4 % of these
+        # 720-order items, 1 % of 120-order ones)
+        assert g.last_fallback_items() < n_all // math.factorial(6) // 10
     per = math.factorial(6)
     for item in (0, 1, 12345, n_all // per // 2, n_all // per - 1):
         got = out[item * per:(item + 1) * per].cpu().numpy()
@@ -138,3 +139,30 @@ def test_edge_sets(ko, case):
     with ko.Gpu.from_set(s) as g:
         g.configure(lanes=1)
         assert np.array_equal(_all(g, s.n), want), case
+
+
+@pytest.mark.parametrize("seed", [14, 21, 31])
+def test_partly_overflowing_sets_full_space(ko, seed):
+    """Sets with many small blocks per SM (148 SMs, 32 block slots, up to 32
+    resident groups per SM) where the one-thread pass runs out of group slots
+    on part of the work items only: the run-length passes must finish exactly
+    those items, every order against the oracle, counts and histogram too."""
+    s = synth.random_set(300 + seed, 8, gpu=(148, 65536, 233472, 64, 32), blk=(100, 1000), c=(1000, 50000))
+    k = s.kernels.copy()
+    k[:, 0] = np.minimum(k[:, 0], 2048)
+    k[:, 1] = 0
+    k[:, 2] = np.minimum(k[:, 2], 2)
+    s = synth.KernelSet(gpu=s.gpu, kernels=k)
+    want = oracle.makespans_idx(s.gpu, s.kernels, first=0, count=40320)
+    h = oracle.heuristic(s.gpu, s.kernels)
+    st = oracle.exhaustive_stats(s.gpu, s.kernels, oracle.makespan(s.gpu, s.kernels, h), makespans=want)
+    with ko.Gpu.from_set(s) as g:
+        g.configure(lanes=1, levels=3)
+        got = _all(g, 8)
+        moved = g.last_fallback_items()
+        r, hist = g.rank_order(h, nbins=4096)
+    assert 0 < moved < 40320 // 24
+    assert np.array_equal(got, want), int(np.argmax(got != want))
+    assert (r["min"], r["max"], r["n_better"], r["n_equal"], r["n_worse"]) == \
+        (st["min"], st["max"], st["n_better"], st["n_equal"], st["n_worse"])
+    assert np.array_equal(hist, st["hist"])
