@@ -144,51 +144,57 @@ def placements_per_exhaustive(kernels) -> int:
     return sum(math.factorial(n - 1) // math.factorial(n - d) for d in range(1, n + 1)) * total_blocks
 
 
-def measured_traffic(workload):
-    """DRAM bytes per launch of the run-length kernel from the committed ncu
-    summary, or None when no summary covers this workload or the kernel's
-    sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", f"fast_kernel_{workload}_dram.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    mb = re.search(r"^- bytes per launch: (\d+)$", text, re.M)
-    mh = re.search(r"^- source sha256 \(ko_fast.cu \+ ko_fast.h\): ([0-9a-f]{64})$", text, re.M)
-    if not mb or not mh:
-        return None
-    return int(mb.group(1)) if source_hash() == mh.group(1) else None
+KERNEL_SOURCES = {"lane_kernel": ("ko_lane.cu", "ko_lane_sim.cuh", "ko_fast.cu", "ko_fast.h"),
+                  "fast_kernel": ("ko_fast.cu", "ko_fast.h")}
 
 
-def measured_counters(workload):
-    """Issue-slot use, active threads per instruction and warp instructions
-    per order of the run-length kernel from the committed ncu summary, or None
-    when no summary covers this workload or the kernel's sources changed since
-    the counters were taken."""
-    path = os.path.join(ROOT, "profiles", f"fast_kernel_{workload}_counters.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    mh = re.search(r"^- source sha256 \(ko_fast.cu \+ ko_fast.h\): ([0-9a-f]{64})$", text, re.M)
-    if not mh or mh.group(1) != source_hash():
-        return None
-    out = {}
-    for key in ("issue_active_pct", "threads_per_inst", "warp_inst_per_order", "case"):
-        m = re.search(rf"^- {key}: (.+)$", text, re.M)
-        if m:
-            v = m.group(1).strip()
-            try:
-                out[key] = float(v)
-            except ValueError:
-                out[key] = v
-    return out or None
-
-
-def source_hash():
+def source_hash(kernel):
+    """SHA-256 of the sources of a simulator kernel (the profile summaries
+    record it; a changed kernel invalidates their counters)."""
     h = hashlib.sha256()
-    for f in ("ko_fast.cu", "ko_fast.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1511_07983_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def profile_fields(kernel, workload, kind):
+    """`- key: value` lines of the committed ncu summary
+    profiles/<kernel>_<workload>_<kind>.md, or None when there is none or the
+    kernel's sources changed since its counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_{kind}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"^- source sha256: ([0-9a-f]{64})$", text, re.M)
+    if not mh or mh.group(1) != source_hash(kernel):
+        return None
+    out = {}
+    for m in re.finditer(r"^- ([a-z_0-9]+): (.+)$", text, re.M):
+        key, v = m.group(1), m.group(2).strip()
+        if key == "source":
+            continue
+        try:
+            out[key] = int(v) if re.fullmatch(r"-?\d+", v) else float(v)
+        except ValueError:
+            out[key] = v
+    return out
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per full launch of the dominant kernel (read + write, from
+    an ncu capture, scaled to the workload as its summary states), or None."""
+    f = profile_fields(kernel, workload, "dram")
+    return int(f["bytes_per_launch"]) if f and "bytes_per_launch" in f else None
+
+
+def measured_counters(kernel, workload):
+    """Issue-slot use, active threads per instruction and warp instructions
+    per order of the dominant kernel from its committed ncu summary, or None."""
+    f = profile_fields(kernel, workload, "counters")
+    if not f:
+        return None
+    return {k: f[k] for k in ("case", "issue_active_pct", "threads_per_inst", "warp_inst_per_order") if k in f}
 
 
 def measured_peaks():
@@ -344,7 +350,8 @@ def run_ours(a):
     placements = placements_per_exhaustive(kset.kernels.tolist())
     kernel_s = statistics.mean(sim_ms) / 1e3
     achieved = placements * OPS_PER_PLACEMENT / kernel_s / 1e9
-    traffic = measured_traffic(a.workload)
+    kernel = "lane_kernel" if ko.ko_get_option(g.h, ko.KO_OPT_LANES) == 1 else "fast_kernel"
+    traffic = measured_traffic(kernel, a.workload)
     cb = cpu_baseline(kset, a.cpu_sample) if world == 1 else None
     sur = None
     if a.surrogate and world == 1:
@@ -367,14 +374,14 @@ def run_ours(a):
                    "levels": ko.ko_get_option(g.h, ko.KO_OPT_LEVELS), "autotune": tune},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
-                     "kernel": "fast_kernel", "kernel_ms": kernel_s * 1e3,
+                     "kernel": kernel, "kernel_ms": kernel_s * 1e3,
                      "placements_per_launch": placements, "ops_per_placement": OPS_PER_PLACEMENT,
                      "peak_from": f"measured: ko_hw_int_peak, {int_ops} 32-bit add/xor/min lane-ops "
                                   f"in {int_ms:.3f} ms on {sm_count} SMs",
                      "peak_clocks": iclk_stats,
                      "issue_peak": issue_gops,
                      "issue_peak_from": f"{sm_count} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz",
-                     "ncu": measured_counters(a.workload)},
+                     "ncu": measured_counters(kernel, a.workload)},
         "cpu_baseline": cb,
         "e2e": {"value": whole_job_rate(n_orders, a.steps, world, e2e_elapsed), "unit": "orders/s",
                 "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,

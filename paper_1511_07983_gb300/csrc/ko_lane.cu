@@ -156,17 +156,17 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                         const uint32_t avail = ~used & all & ~((2u << old) - 1u);
                         if (avail) {
                             cand = __ffs((int)avail) - 1;
-                            // streaming loads: the slab must not evict the set's constants from L1
+                            // cached in L2 only: the slab stays out of L1, where the set's constants live
                             const uint4 *src = reinterpret_cast<const uint4 *>(slab + (depth - d0) * kSaveWords);
 #pragma unroll 13
                             for (int f = 0; f < kWords / 4; f++) {
-                                const uint4 v = __ldcs(src + f);
+                                const uint4 v = __ldcg(src + f);
                                 sim.W(4 * f) = v.x; sim.W(4 * f + 1) = v.y; sim.W(4 * f + 2) = v.z; sim.W(4 * f + 3) = v.w;
                             }
                             uint32_t r[kRegWords];
 #pragma unroll
                             for (int f = 0; f < kRegWords / 4; f++) {
-                                const uint4 v = __ldcs(src + kWords / 4 + f);
+                                const uint4 v = __ldcg(src + kWords / 4 + f);
                                 r[4 * f] = v.x; r[4 * f + 1] = v.y; r[4 * f + 2] = v.z; r[4 * f + 3] = v.w;
                             }
                             sim.regs_in(r);
@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
                         uint4 *dst = reinterpret_cast<uint4 *>(slab + (depth - d0) * kSaveWords);
 #pragma unroll 13
                         for (int f = 0; f < kWords / 4; f++)
-                            __stcs(dst + f, make_uint4(sim.W(4 * f), sim.W(4 * f + 1), sim.W(4 * f + 2), sim.W(4 * f + 3)));
+                            __stcg(dst + f, make_uint4(sim.W(4 * f), sim.W(4 * f + 1), sim.W(4 * f + 2), sim.W(4 * f + 3)));
                         uint32_t r[kRegWords];
                         sim.regs_out(r);
 #pragma unroll
                         for (int f = 0; f < kRegWords / 4; f++)
-                            __stcs(dst + kWords / 4 + f, make_uint4(r[4 * f], r[4 * f + 1], r[4 * f + 2], r[4 * f + 3]));
+                            __stcg(dst + kWords / 4 + f, make_uint4(r[4 * f], r[4 * f + 1], r[4 * f + 2], r[4 * f + 3]));
                     }
                     phase = PH_NEXT;
                 }

@@ -216,9 +216,16 @@ struct LaneSim {
         const KParam q = kl.full(k);
         hk = k; hr = q.r; hs = q.s; hw = q.w; hc = q.c; hm = q.m;
         hpk = (uint32_t)q.r | (1u << 19) | ((uint32_t)q.w << 25);
+        // quot63 corrects its estimate exactly, so an approximate reciprocal will do
+#ifdef __CUDA_ARCH__
+        frr = __fdividef(1.0f, (float)q.r);
+        frw = __fdividef(1.0f, (float)q.w);
+        frs = q.s > 0 ? __fdividef(1.0f, (float)q.s) : 0.0f;
+#else
         frr = 1.0f / (float)q.r;
         frw = 1.0f / (float)q.w;
         frs = q.s > 0 ? 1.0f / (float)q.s : 0.0f;
+#endif
     }
 
     // Blocks of the head kernel one SM of run j still takes.
@@ -317,13 +324,16 @@ struct LaneSim {
                               (int)(u >> 25) + hw <= L.W && (int)W(W_RS + j) + hs <= L.Sh;
             room |= (fits ? 1u : 0u) << j;
         }
+        uint32_t take = 0;
         for (uint32_t e = room; e; e &= e - 1) {
             const int j = ffs32(e);
             const int c = cap(j);
             caps.set(j, c);
             ctotal += (int)(W(W_RB + j) >> 16) * c;
             cmax = c > cmax ? c : cmax;
+            take |= (c > 0 ? 1u : 0u) << j;
         }
+        celig = take;  // the placement steps visit only runs that take blocks
     }
 
     // Every SM of the offered runs takes its full capacity (ctotal <= left);
