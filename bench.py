@@ -406,88 +406,104 @@ def percentile_of(best, ref):
     return 100.0 * float(np.count_nonzero(ref >= best)) / ref.size
 
 
-def surrogate_experiment(seed=7, train_sets=1221, pairs=8192, steps=2500, batch=4096,
-                         test_sets=32, n_cand=1 << 20, top_k=1024, rounds=12, beam=8,
-                         ref_orders=1 << 20):
-    """Surrogate-guided search vs plain random-order search at equal GPU time.
-
-    The network is trained only on enumerable sets: train_sets seeded sets
-    with N in 6..12 (13-, 15- or 148-SM GPUs), pairs uniform random orders of
-    each labelled exactly by the simulator (10.0M pairs), steps Adam steps of
-    `batch` pairs (about one epoch).  On each of test_sets held-out sets with N
-    in 16..24 (too large to enumerate) the surrogate screens n_cand random
-    candidates, rescores its top_k exactly and runs `rounds` of network-ranked
-    local search around a beam of the best exact orders (ko_surrogate_search);
-    plain search simulates as many uniform random orders as fit in the
-    surrogate's measured GPU time.  Wins are counted on the exact makespans
-    of the two best orders.  Exact steepest descent from Algorithm 1's order
-    (ko_local_search, no model, its own time) is reported beside them, and
-    every best order is also ranked against the exact makespans of ref_orders
-    seeded uniform orders (context: at these sizes that sample's best is
-    itself far from optimal)."""
-    import numpy as np
+def train_surrogate(kind, seed=7, train_sets=1221, pairs=8192, steps=2500, batch=4096):
+    """Train the MLP on exactly simulated uniform orders: kind "small" uses
+    only enumerable sets (N 6..12, as the scope specifies), "mixed" half of
+    them and half N 16..24 sets (disjoint seeds from the test sets), kind
+    "untrained" returns the initial weights (the search's control)."""
     from paper_1511_07983_gb300 import ko, synth
-    t0 = time.perf_counter()
-    train = [synth.gen_set("train", 1000 + i) for i in range(train_sets)]
-    assert max(k.n for k in train) <= 12
-    gpus = [ko.Gpu.from_set(k) for k in train]
     model = ko.Model(seed=seed)
+    if kind == "untrained":
+        return model, {"kind": kind}
+    if kind == "small":
+        sets = [synth.gen_set("train", 1000 + i) for i in range(train_sets)]
+    else:
+        half = train_sets // 2
+        sets = [synth.gen_set("train", 1000 + i) for i in range(train_sets - half)]
+        sets += [synth.gen_set("large", 1000 + i) for i in range(half)]
+    gpus = [ko.Gpu.from_set(k) for k in sets]
+    t0 = time.perf_counter()
     curve = model.train(gpus, pairs_per_set=pairs, steps=steps, batch=batch, lr=1e-3, seed=seed)
+    train_s = time.perf_counter() - t0
     for g in gpus:
         g.close()
-    train_s = time.perf_counter() - t0
-    rows = []
+    return model, {"kind": kind, "train_sets": len(sets), "train_n": f"{min(k.n for k in sets)}..{max(k.n for k in sets)}",
+                   "train_pairs": len(sets) * pairs, "train_steps": steps, "batch": batch,
+                   "train_s": round(train_s, 2), "final_loss": float(curve[-50:].mean())}
+
+
+def surrogate_experiment(seed=7, test_sets=32, n_cand=1 << 18, top_k=1024, rounds=6, beam=8, polish=64,
+                         ref_orders=1 << 20):
+    """The learned part on sets too large to enumerate (N 16..24), every
+    reported makespan exact.  For each network -- trained on N <= 12 sets only
+    (the specified transfer), trained with N <= 24 labels (the variant for a
+    model that does not transfer), and untrained (control) -- on each of
+    test_sets held-out sets:
+      * screening at equal exact budgets: the best of the network's top_k out
+        of n_cand random candidates vs the best of top_k uniform orders;
+      * guided search (ko_surrogate_search: screening, then `rounds` rounds of
+        network-ranked neighbours around a beam of the best exact orders) vs
+        plain uniform random search given the same measured GPU time, without
+        and with the exact steepest-descent polish (KO_MODEL_OPT_POLISH);
+    wins are counted on exact makespans.  Exact local search from Algorithm
+    1's order (no model, its own time) and ranks against ref_orders seeded
+    uniform orders are reported beside them."""
+    import numpy as np
+    from paper_1511_07983_gb300 import ko, synth
+    tests = [synth.gen_set("large", j) for j in range(test_sets)]
     rng = np.random.default_rng(seed)
-    for j in range(test_sets):
-        ks = synth.gen_set("large", j)
+    base = []
+    for j, ks in enumerate(tests):
         with ko.Gpu.from_set(ks) as g:
             ref_rows = np.argsort(rng.random((ref_orders, ks.n)), axis=1).astype(np.int8)
             ref = g.eval_orders(orders=ref_rows)
-            _, s_best, s_ms = model.search(g, n_cand=n_cand, top_k=top_k, rounds=rounds, beam=beam,
-                                           seed=seed + j)
-            _, _, cal_ms = ko.ko_random_search(g, 1 << 16, seed=99 + j)
-            n_plain = max(1, int((1 << 16) * s_ms / max(cal_ms, 1e-3)))
-            _, p_best, p_ms = ko.ko_random_search(g, n_plain, seed=seed + 100 + j)
             h_ms = int(g.eval_orders(orders=np.array([g.heuristic_order()], dtype=np.int8))[0])
             _, l_best, _, l_orders, l_ms = g.local_search(moves=True)
-            rows.append({"n": ks.n, "n_sm": ks.gpu[0], "surrogate_ms": s_ms, "plain_ms": p_ms,
-                         "plain_orders": n_plain, "local_search_ms": l_ms, "local_search_orders": l_orders,
-                         "makespans": {"surrogate": int(s_best), "plain": int(p_best), "local_search": int(l_best),
-                                       "heuristic": h_ms},
-                         "surrogate_pct": percentile_of(s_best, ref),
-                         "plain_pct": percentile_of(p_best, ref),
-                         "local_search_pct": percentile_of(l_best, ref),
-                         "heuristic_pct": percentile_of(h_ms, ref)})
-    model.close()
-    mean = lambda k: sum(r[k] for r in rows) / len(rows)
-    ms = lambda r, k: r["makespans"][k]
-    return {"test_sets": len(rows), "train_sets": train_sets, "train_n": "6..12",
-            "train_pairs": train_sets * pairs, "train_steps": steps, "batch": batch,
-            "train_s": round(train_s, 2), "final_loss": float(curve[-50:].mean()),
-            "candidates": n_cand, "top_k": top_k, "rounds": rounds, "beam": beam,
-            # wins on exact makespans, surrogate vs plain random search at equal GPU time
-            "surrogate_vs_plain_makespan": {
-                "lower": sum(ms(r, "surrogate") < ms(r, "plain") for r in rows),
-                "equal": sum(ms(r, "surrogate") == ms(r, "plain") for r in rows),
-                "higher": sum(ms(r, "surrogate") > ms(r, "plain") for r in rows)},
-            "surrogate_vs_plain_gain_mean": mean_gain(rows, "plain", "surrogate"),
-            "reference_orders": ref_orders,
-            "surrogate_percentile_mean": mean("surrogate_pct"),
-            "plain_percentile_mean": mean("plain_pct"),
-            "heuristic_percentile_mean": mean("heuristic_pct"),
-            # exact steepest descent from Algorithm 1 (swaps + moves): no model, its own time
-            "local_search_percentile_mean": mean("local_search_pct"),
-            "local_search_ms_mean": mean("local_search_ms"),
-            "surrogate_vs_local_search_makespan": {
-                "lower": sum(ms(r, "surrogate") < ms(r, "local_search") for r in rows),
-                "equal": sum(ms(r, "surrogate") == ms(r, "local_search") for r in rows),
-                "higher": sum(ms(r, "surrogate") > ms(r, "local_search") for r in rows)},
-            "per_set": rows}
+            _, r_best, _ = ko.ko_random_search(g, top_k, seed=seed + 200 + j)
+            _, _, cal_ms = ko.ko_random_search(g, 1 << 16, seed=99 + j)
+        base.append({"n": ks.n, "n_sm": ks.gpu[0], "ref": ref, "heuristic": h_ms, "local_search": int(l_best),
+                     "local_search_ms": l_ms, "random_budget": int(r_best), "cal_ms": cal_ms})
+    out = {"test_sets": test_sets, "candidates": n_cand, "top_k": top_k, "rounds": rounds, "beam": beam,
+           "polish_steps": polish, "reference_orders": ref_orders,
+           "heuristic_percentile_mean": float(np.mean([percentile_of(b["heuristic"], b["ref"]) for b in base])),
+           "local_search_percentile_mean": float(np.mean([percentile_of(b["local_search"], b["ref"]) for b in base])),
+           "local_search_ms_mean": float(np.mean([b["local_search_ms"] for b in base]))}
+    for kind in ("small", "mixed", "untrained"):
+        model, info = train_surrogate(kind, seed=seed)
+        res = dict(info)
+        if kind != "untrained":
+            scr = []
+            for j, ks in enumerate(tests):
+                with ko.Gpu.from_set(ks) as g:
+                    _, sb, _ = model.propose(g, n_cand=1 << 20, top_k=top_k, seed=seed + j)
+                scr.append(int(sb))
+            res["screening_vs_random_at_equal_exact_budget"] = wins(scr, [b["random_budget"] for b in base])
+        for pol in (0, polish):
+            model.set_polish(pol)
+            guided, plain, pcts = [], [], []
+            for j, ks in enumerate(tests):
+                with ko.Gpu.from_set(ks) as g:
+                    _, sb, s_ms = model.search(g, n_cand=n_cand, top_k=top_k, rounds=rounds, beam=beam, seed=seed + j)
+                    n_plain = max(1, int((1 << 16) * s_ms / max(base[j]["cal_ms"], 1e-3)))
+                    _, pb, _ = ko.ko_random_search(g, n_plain, seed=seed + 100 + j)
+                guided.append(int(sb))
+                plain.append(int(pb))
+                pcts.append((percentile_of(sb, base[j]["ref"]), percentile_of(pb, base[j]["ref"])))
+            key = "guided" if pol == 0 else "guided_polished"
+            res[key + "_vs_plain_at_equal_gpu_time"] = wins(guided, plain)
+            res[key + "_vs_local_search"] = wins(guided, [b["local_search"] for b in base])
+            res[key + "_percentile_mean"] = float(np.mean([p[0] for p in pcts]))
+            res[key + "_plain_percentile_mean"] = float(np.mean([p[1] for p in pcts]))
+        model.close()
+        out[kind] = res
+    return out
 
 
-def mean_gain(rows, base, new):
-    """Mean relative makespan reduction of `new` over `base` (exact makespans)."""
-    return sum((r["makespans"][base] - r["makespans"][new]) / r["makespans"][base] for r in rows) / len(rows)
+def wins(a, b):
+    """Exact-makespan comparison of two lists of best makespans (lower wins)."""
+    return {"lower": sum(x < y for x, y in zip(a, b)), "equal": sum(x == y for x, y in zip(a, b)),
+            "higher": sum(x > y for x, y in zip(a, b)),
+            "mean_gain": sum((y - x) / y for x, y in zip(a, b)) / len(a)}
 
 
 BATCH_WORKLOADS = {"sets10": (64, NBINS), "batched": (4096, 0)}

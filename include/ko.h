@@ -363,9 +363,11 @@ ko_status ko_surrogate_propose(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t t
  * beam of the `beam` (1..64) best exact orders; each of `rounds` (0..1024)
  * rounds scores every swap of two positions and every move of one kernel to
  * another position of each beam order with the network, rescores the 256
- * best exactly and keeps the `beam` best distinct orders.  Returns the best
- * exact order found (host, N ids); gpu_ms = device-timeline duration of the
- * whole search including the host's per-round bookkeeping. */
+ * best exactly and keeps the `beam` best distinct orders; then an exact
+ * steepest descent from the best order found (KO_MODEL_OPT_POLISH steps at
+ * most).  Returns the best exact order found (host, N ids); gpu_ms =
+ * device-timeline duration of the whole search including the host's
+ * per-round and per-step bookkeeping. */
 ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t top_k, int32_t rounds,
                               int32_t beam, uint64_t seed, int32_t *best_order, int64_t *best_makespan,
                               double *gpu_ms, void *stream);
@@ -412,6 +414,12 @@ ko_status ko_local_search(ko_gpu *g, const int32_t *start, int32_t moves, int32_
  * fixed-order reduction) or on warp-level mma.sync (0).  The two paths
  * accumulate in different orders, so their gradients agree to rounding. */
 #define KO_MODEL_OPT_TC_TRAIN 3
+/* KO_MODEL_OPT_POLISH: after its rounds, ko_surrogate_search walks an exact
+ * steepest descent (every swap and every single move simulated, as
+ * ko_local_search does) from the best exact order it found, for at most this
+ * many steps (0..2^20, default 64; 0 = none), inside its timed region.  The
+ * network proposes; the simulator alone accepts. */
+#define KO_MODEL_OPT_POLISH 4
 ko_status ko_model_set_option(ko_model *m, int32_t key, int64_t value);
 
 void ko_model_destroy(ko_model *m);

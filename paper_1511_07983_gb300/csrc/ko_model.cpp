@@ -85,6 +85,7 @@ struct ko_model {
     size_t wg_bytes = 0;
     int chunk = 262144;        // candidate rows per forward pass of the proposal paths
     int *tc_err = nullptr;     // device flag: a tcgen05 completion wait gave up
+    int polish = 64;           // exact descent steps after a guided search (0: none)
 
     void free_acts()
     {
@@ -358,6 +359,11 @@ ko_status ko_model_option(ko_model *md, int key, long long value)
     if (key == KO_MODEL_OPT_CHUNK) {
         if (value < 1024 || value > (1 << 22) || value % 1024) return KO_ERR_ARG;
         md->chunk = (int)value;
+        return KO_OK;
+    }
+    if (key == KO_MODEL_OPT_POLISH) {
+        if (value < 0 || value > (1 << 20)) return KO_ERR_ARG;
+        md->polish = (int)value;
         return KO_OK;
     }
     return KO_ERR_ARG;
@@ -713,6 +719,21 @@ ko_status ko_model_search_set(ko_model *md, const KoSet &h, long long n_cand, in
             if (!s) s = cuda_ok(ko_mlp_gather_rows(nb, kMaxK, top_idx, kk, top_rows, st));
             if (!s) s = exact_rows(&md->fast, tb.sets, h, 0, top_rows, kk, top_ms, d_chunk, st);
             if (!s) s = collect(kk);
+        }
+        // exact steepest descent from the best exact order (the simulator alone decides)
+        if (!s && md->polish > 0 && !pool.empty()) {
+            if (cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;
+            std::vector<int32_t> start(n), out(n);
+            for (int i = 0; i < n; i++) start[i] = pool[0].row[i];
+            int64_t pms = -1, evals = 0;
+            int32_t steps = 0;
+            double lms = 0.0;
+            if (!s) s = ko_local_search_set(&md->fast, h, start.data(), true, md->polish, out.data(), &pms, &steps,
+                                            &evals, &lms, st);
+            if (!s && pms >= 0 && pms < pool[0].ms) {
+                pool[0].ms = pms;
+                for (int i = 0; i < n; i++) pool[0].row[i] = (int8_t)out[i];
+            }
         }
         cudaEventRecord(e1, st);
         if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = KO_ERR_CUDA;

@@ -483,6 +483,10 @@ class Model:
         """Training GEMMs on tcgen05 (True) or warp-level mma.sync (False)."""
         _check(lib().ko_model_set_option(self.m, 3, int(bool(on))), "ko_model_set_option")
 
+    def set_polish(self, steps: int):
+        """Exact descent steps after a guided search (KO_MODEL_OPT_POLISH; 0 = none)."""
+        _check(lib().ko_model_set_option(self.m, 4, int(steps)), "ko_model_set_option")
+
     def set_chunk(self, rows: int):
         """Candidate rows per forward pass of propose/search (multiple of 1024)."""
         _check(lib().ko_model_set_option(self.m, 2, int(rows)), "ko_model_set_option")
