@@ -54,22 +54,31 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
 
 def test_traffic_figure_only_for_unchanged_kernel_sources(tmp_path, monkeypatch):
+    """The benchmark reports a profile's DRAM bytes and counters only while
+    the profiled kernel's sources are the ones the summary names."""
     import bench
     prof = tmp_path / "profiles"
     csrc = tmp_path / "paper_1511_07983_gb300" / "csrc"
     prof.mkdir()
     csrc.mkdir(parents=True)
-    (csrc / "ko_fast.cu").write_text("kernel A")
-    (csrc / "ko_fast.h").write_text("header")
+    names = bench.KERNEL_SOURCES["lane_kernel"]
+    for i, f in enumerate(names):
+        (csrc / f).write_text(f"source {i}")
     import hashlib
-    good = hashlib.sha256(b"kernel A" + b"header").hexdigest()
-    (prof / "fast_kernel_w_dram.md").write_text(
-        "x\n- bytes per launch: 1234\n- source sha256 (ko_fast.cu + ko_fast.h): " + good + "\n")
+    good = hashlib.sha256(b"".join(f"source {i}".encode() for i in range(len(names)))).hexdigest()
+    (prof / "lane_kernel_w_dram.md").write_text(
+        "x\n- bytes_per_launch: 1234\n- source sha256: " + good + "\n")
+    (prof / "lane_kernel_w_counters.md").write_text(
+        "- case: n11\n- issue_active_pct: 40.1\n- threads_per_inst: 7.77\n- source sha256: " + good + "\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic("w") == 1234
-    assert bench.measured_traffic("other") is None
-    (csrc / "ko_fast.cu").write_text("kernel B")
-    assert bench.measured_traffic("w") is None
+    assert bench.measured_traffic("lane_kernel", "w") == 1234
+    assert bench.measured_counters("lane_kernel", "w") == {"case": "n11", "issue_active_pct": 40.1,
+                                                           "threads_per_inst": 7.77}
+    assert bench.measured_traffic("lane_kernel", "other") is None
+    assert bench.measured_traffic("fast_kernel", "w") is None
+    (csrc / names[0]).write_text("changed")
+    assert bench.measured_traffic("lane_kernel", "w") is None
+    assert bench.measured_counters("lane_kernel", "w") is None
 
 
 def test_reference_arm_line_on_rank0(monkeypatch, capsys):
