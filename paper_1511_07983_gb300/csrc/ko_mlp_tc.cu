@@ -13,10 +13,12 @@
 //                          split-K, one 256-wide K slice per CTA, FP32 partial
 //                          tiles to a workspace; wgrad_reduce_kernel sums the
 //                          slices in a fixed order (deterministic).
-//   tc_tma_kernel          the MODE 0 layer with both operands loaded by TMA
-//                          (cp.async.bulk.tensor), the default for inference.
+//   tc_ws_kernel           the MODE 0 layer, warp-specialised: TMA producer,
+//                          MMA issuer and epilogue warps over a ring of
+//                          128-byte-swizzled A stages and two TMEM
+//                          accumulators (the default for inference).
 //
-//  * Operands sit in shared memory in the no-swizzle core-matrix layout: a
+//  * The cp.async kernels keep operands in the no-swizzle core-matrix layout: a
 //    core matrix is 8 rows x 16 bytes; core matrices adjacent along K are
 //    LBO = 128 bytes apart, adjacent 8-row groups SBO = (K/8) * 128 bytes
 //    apart.  Fills map 8 consecutive threads to one core matrix, so a warp
@@ -34,8 +36,8 @@
 //    the 32 x 32 piece as one word per value with a row stride of 33 words,
 //    which makes both the row-wise and the column-wise reads conflict-free,
 //    and writes out and out_t (64 contiguous bytes per lane) from it.
-// Shared memory (at most 226 KB) keeps one CTA per SM, so the 256-column TMEM
-// allocation never waits for another CTA.
+// Shared memory (at most 226 KB) keeps one CTA per SM, so a TMEM allocation
+// (256 columns; 512 in tc_ws_kernel) never waits for another CTA.
 #include <cstdint>
 #include <cstring>
 
@@ -61,6 +63,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Descriptor of a K-major operand in the 128-byte swizzled layout that TMA
+// writes with CU_TENSOR_MAP_SWIZZLE_128B: rows of 64 BF16 (128 bytes), 8-row
+// atoms of 1024 bytes (SBO), layout type 2 in bits 61-63.  A K = 16 step inside
+// the atom starts 32 bytes further (the hardware applies the swizzle to the
+// computed addresses).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
@@ -285,15 +298,7 @@ tc_layer_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__ Wt,
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
 }
 
-// Inference layer (MODE 0 arithmetic) with operands loaded by TMA.  A 2-D box
-// of 8 elements (16 bytes) x R rows lands one K chunk of R rows as R x 16
-// contiguous bytes: a column of R / 8 core matrices, so the operand layout is
-// K-chunk-major (chunk c at c * R * 16 bytes) and the MMA descriptors take
-// LBO = R * 16 bytes (adjacent along K) and SBO = 128 bytes (adjacent 8-row
-// groups).  One thread issues K/8 box copies per operand, counted in bytes on
-// an mbarrier (expect_tx); the weights (R = 256) and the first A tile (R = 128)
-// arrive together, each later A tile as soon as the previous tile's MMAs have
-// retired.  Epilogue as tc_layer_kernel<0>.
+// One 2-D TMA box copy into shared memory, completion counted in bytes on mbar.
 __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *mbar)
 {
     asm volatile(
@@ -307,77 +312,207 @@ __device__ __forceinline__ void expect_bytes(uint64_t *mbar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(mbar)), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreadsTc, 1)
-tc_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int K, int tiles,
-              const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
+// Warp-specialised inference layer (MODE 0 arithmetic): the A operand streams
+// through a ring of stages, each a 128-row x 64-element K chunk (16 KB, one
+// TMA box in the 128-byte swizzled layout; the weights are K/64 such boxes of
+// 256 rows), and the accumulator is
+// double-buffered in TMEM (two 256-column accumulators), so that loads, MMAs
+// and epilogues of consecutive tiles overlap:
+//   warp E (one thread)  TMA producer: weights once, then every A chunk as soon
+//                        as its stage is empty;
+//   warp E+1 (one thread) MMA issuer: per chunk four K = 16 MMAs into the
+//                        tile's accumulator, a commit that empties the stage,
+//                        and after a tile's last chunk a commit that marks the
+//                        accumulator full;
+//   warps 0..E-1         epilogue (as tc_layer_kernel<0>; E = kEpiWarps, warp
+//                        w reads TMEM lanes 32 (w % 4).. and kEpiCols columns),
+//                        then one arrival per warp that frees the accumulator.
+// mbarriers: full/empty per stage, full/free per accumulator, one for the
+// weights.  Chunk n of this CTA's stream uses stage n % stages for the
+// (n / stages)-th time; tile i uses accumulator i % 2 for the (i / 2)-th time;
+// a wait for the u-th completion of a barrier tests phase parity u & 1.  Every
+// wait is bounded and checks a shared abort flag, so a failed wait stops all
+// roles (error flag set) instead of leaving them spinning.
+constexpr int kChunkK = 64;                               // K elements per stage
+constexpr uint32_t kStageBytes = kTileM * kChunkK * 2;    // 16 KB
+constexpr int kMaxStages = 8;
+#ifndef KO_TC_EPI_WARPS
+#define KO_TC_EPI_WARPS 16
+#endif
+constexpr int kEpiWarps = KO_TC_EPI_WARPS;                // 4 per TMEM lane quarter at 16
+constexpr int kEpiCols = kTileN / (kEpiWarps / 4);        // accumulator columns per epilogue warp
+constexpr int kWsThreads = (kEpiWarps + 2) * 32;          // epilogue warps + producer + MMA warps
+static_assert(kEpiWarps % 4 == 0 && kEpiCols % 32 == 0, "epilogue warps cover the lane quarters evenly");
+
+// Bounded wait for the completion of parity `phase` of `mbar`; gives up (sets
+// *abort and *err) after kSpinLimit polls or when another role has aborted.
+__device__ __forceinline__ bool ws_wait(uint64_t *mbar, uint32_t phase, volatile int *abort, int *err)
+{
+    uint32_t done = 0;
+    for (uint32_t spin = 0; spin < kSpinLimit && !done; spin++) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(saddr(mbar)), "r"(phase));
+        if (!done && (spin & 255u) == 255u && *abort) break;
+    }
+    if (!done) {
+        *abort = 1;
+        atomicExch(err, 1);
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(mbar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        saddr(mbar)));
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+tc_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int K, int tiles,
+             int stages, const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar_mma, mbar_load;
+    __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
+    __shared__ __align__(8) uint64_t bar_acc[2], bar_free[2], bar_w, bar_drain;
     __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, col0 = (warp >> 2) * (kTileN / 2);
-    const int kc = K / 8;
-    uint8_t *sa = smem;                              // kc chunks x 128 rows x 16 B
-    uint8_t *sb = smem + (size_t)kTileM * K * 2;     // kc chunks x 256 rows x 16 B
-    float *sbias = (float *)(sb + (size_t)kTileN * K * 2);
-    uint32_t *stage = (uint32_t *)(sbias + kTileN) + warp * 32 * kStageRowWords;
+    const int kchunks = K / kChunkK;
+    uint8_t *sw = smem;                                   // K/8 chunks x 256 rows x 16 B
+    uint8_t *ring = smem + (size_t)kTileN * K * 2;        // stages x (8 chunks x 128 rows x 16 B)
+    float *sbias = (float *)(ring + (size_t)stages * kStageBytes);
+    const int ntiles = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // swizzled TMA destinations and the MMA atoms need 1024-byte aligned stages
+    if (saddr(smem) & 1023u) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(saddr(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(saddr(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar_mma)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar_load)));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-    }
-    __syncthreads();
-    if (tid == 0 && blockIdx.x < tiles) {
-        expect_bytes(&mbar_load, (uint32_t)((kTileN + kTileM) * K * 2));
-        for (int c = 0; c < kc; c++) {
-            tma_box(saddr(sb) + (uint32_t)(c * kTileN * 16), &tmW, c * 8, 0, &mbar_load);
-            tma_box(saddr(sa) + (uint32_t)(c * kTileM * 16), &tmA, c * 8, blockIdx.x * kTileM, &mbar_load);
+        for (int s = 0; s < stages; s++) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
         }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar_acc[b], 1);
+            mbar_init(&bar_free[b], kEpiWarps);
+        }
+        mbar_init(&bar_w, 1);
+        mbar_init(&bar_drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
     for (int i = tid; i < kTileN; i += blockDim.x) sbias[i] = bias[i];
     tc_fence_sync();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = instr_desc(kTileM, kTileN);
-    bool ok = true;
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, phase ^= 1u) {
-        const int m0 = tile * kTileM;
-        if (!tc_wait(&mbar_load, phase, err)) { ok = false; break; }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            for (int k = 0; k < K / 16; k++) {
-                // a 16-wide K step covers chunks 2k and 2k + 1
-                const uint64_t ad = smem_desc(saddr(sa) + (uint32_t)(2 * k * kTileM * 16), kTileM * 16, 128u);
-                const uint64_t bd = smem_desc(saddr(sb) + (uint32_t)(2 * k * kTileN * 16), kTileN * 16, 128u);
-                const uint32_t acc = k > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+
+    if (warp == kEpiWarps) {
+        // TMA producer
+        if (lane == 0 && ntiles > 0) {
+            expect_bytes(&bar_w, (uint32_t)(kTileN * K * 2));
+            for (int c = 0; c < kchunks; c++)
+                tma_box(saddr(sw) + (uint32_t)(c * kTileN * kChunkK * 2), &tmW, c * kChunkK, 0, &bar_w);
+            int n = 0;
+            bool ok = true;
+            for (int i = 0; i < ntiles && ok; i++) {
+                const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kTileM;
+                for (int k = 0; k < kchunks; k++, n++) {
+                    const int s = n % stages;
+                    const uint32_t u = (uint32_t)(n / stages);
+                    if (u > 0 && !ws_wait(&bar_empty[s], (u - 1u) & 1u, &abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = saddr(ring) + (uint32_t)s * kStageBytes;
+                    expect_bytes(&bar_full[s], kStageBytes);
+                    tma_box(dst, &tmA, k * kChunkK, row, &bar_full[s]);
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                saddr(&mbar_mma)));
+            if (!ok) {
+                // copies still in flight land before the CTA exits: the last load of each stage
+                int zero = 0;
+                for (int s = 0; s < stages && s < n; s++) {
+                    const int last = n - 1 - ((n - 1 - s) % stages);
+                    ws_wait(&bar_full[s], (uint32_t)(last / stages) & 1u, &zero, err);
+                }
+                int wz = 0;
+                ws_wait(&bar_w, 0u, &wz, err);
+            }
         }
-        if (!tc_wait(&mbar_mma, phase, err)) {
-            ok = false;
-        } else {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            // the MMAs have read the A tile: fetch the next one under the epilogue
-            const int tn = tile + (int)gridDim.x;
-            if (tid == 0 && tn < tiles) {
-                expect_bytes(&mbar_load, (uint32_t)(kTileM * K * 2));
-                for (int c = 0; c < kc; c++)
-                    tma_box(saddr(sa) + (uint32_t)(c * kTileM * 16), &tmA, c * 8, tn * kTileM, &mbar_load);
+    } else if (warp == kEpiWarps + 1) {
+        // MMA issuer
+        if (lane == 0 && ntiles > 0) {
+            const uint32_t idesc = instr_desc(kTileM, kTileN);
+            bool ok = ws_wait(&bar_w, 0u, &abort_flag, err);
+            int n = 0;
+            for (int i = 0; i < ntiles && ok; i++) {
+                const int b = i & 1;
+                if (i >= 2 && !ws_wait(&bar_free[b], (uint32_t)((i >> 1) - 1) & 1u, &abort_flag, err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                const uint32_t acc_t = tmem + (uint32_t)(b * kTileN);
+                for (int k = 0; k < kchunks; k++, n++) {
+                    const int s = n % stages;
+                    if (!ws_wait(&bar_full[s], (uint32_t)(n / stages) & 1u, &abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                    const uint32_t a0 = saddr(ring) + (uint32_t)s * kStageBytes;
+                    for (int j = 0; j < kChunkK / 16; j++) {
+                        // a 16-wide K step covers two 8-element chunks
+                        const int kk = k * (kChunkK / 16) + j;
+                        const uint64_t ad = smem_desc_sw128(a0 + (uint32_t)(j * 32));
+                        const uint64_t bd = smem_desc_sw128(saddr(sw) + (uint32_t)(k * kTileN * kChunkK * 2 + j * 32));
+                        const uint32_t accum = kk > 0 ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+                    mma_commit(&bar_empty[s]);   // the stage is free once these MMAs have read it
+                }
+                if (ok) mma_commit(&bar_acc[b]);  // the tile's accumulator is complete
             }
-            const int row0 = m0 + quarter * 32;
-            for (int c0 = col0; c0 < col0 + kTileN / 2; c0 += 32) {
+            if (!ok) {
+                // MMAs in flight retire before the accumulators are freed
+                mma_commit(&bar_drain);
+                int zero = 0;
+                ws_wait(&bar_drain, 0u, &zero, err);
+            }
+        }
+    } else {
+        // epilogue: warps w, w + 4, ... share TMEM lanes 32 (w % 4).., kEpiCols columns each
+        const int quarter = warp & 3, col0 = (warp >> 2) * kEpiCols;
+        uint32_t *stage = (uint32_t *)(sbias + kTileN) + warp * 32 * kStageRowWords;
+        for (int i = 0; i < ntiles; i++) {
+            const int b = i & 1;
+            const bool got = ws_wait(&bar_acc[b], (uint32_t)(i >> 1) & 1u, &abort_flag, err);
+            if (!__all_sync(0xffffffffu, got)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const int row0 = ((int)blockIdx.x + i * (int)gridDim.x) * kTileM + quarter * 32;
+            const uint32_t acc_t = tmem + (uint32_t)(b * kTileN);
+            for (int c0 = col0; c0 < col0 + kEpiCols; c0 += 32) {
                 uint32_t v[32];
-                tc_ld32(tmem, quarter, c0, v);
+                tc_ld32(acc_t, quarter, c0, v);
                 uint32_t packed[16];
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
@@ -398,14 +533,13 @@ tc_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
                 __syncwarp();
             }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_free[b]);
         }
-        // every warp has drained the accumulator before the next tile's MMAs overwrite it
-        tc_fence_sync();
     }
-    // a load still in flight (only after a failed wait) must land before the CTA exits
-    if (!ok && tid == 0) tc_wait(&mbar_load, phase, err);
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once.
@@ -426,17 +560,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// rows x K BF16 matrix (row-major, K contiguous), boxes of 8 x box_rows.
-bool encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, int K, int box_rows)
+// rows x K BF16 matrix (row-major, K contiguous), boxes of 64 x box_rows in
+// the 128-byte swizzled layout (K a multiple of 64).
+bool encode_operand_sw128(CUtensorMap *map, const uint16_t *base, long long rows, int K, int box_rows)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || ((uintptr_t)base & 15u) || (K * 2) % 16) return false;
+    if (!enc || ((uintptr_t)base & 15u) || K % 64) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1u, 1u};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -540,21 +675,31 @@ cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K,
 {
     if (M % kTileM || (K != 192 && K != 256)) return cudaErrorInvalidValue;
     CUtensorMap tma, tmw;
-    const size_t smem = (size_t)(kTileM + kTileN) * K * 2 + sizeof(float) * kTileN +
-                        (kThreadsTc / 32) * 32 * kStageRowWords * sizeof(uint32_t);
-    if ((long long)smem > (long long)max_dyn_smem() || !encode_operand(&tma, A, M, K, kTileM) ||
-        !encode_operand(&tmw, Wt, kTileN, K, kTileN))
-        return launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
-    cudaError_t e = cudaFuncSetAttribute(tc_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = M / kTileM;
-    const int grid = tiles < sms ? tiles : sms;
-    tc_tma_kernel<<<grid, kThreadsTc, smem, st>>>(tma, tmw, K, tiles, bias, out, err);
-    ko_count_launch();
-    return cudaGetLastError();
+    {
+        // warp-specialised kernel: as many 16 KB A stages as fit beside the weights (1 KB kept
+        // for the static barriers)
+        const size_t fixed = (size_t)kTileN * K * 2 + sizeof(float) * kTileN +
+                             (size_t)kEpiWarps * 32 * kStageRowWords * sizeof(uint32_t);
+        const long long room = (long long)max_dyn_smem() - 1024 - (long long)fixed;
+        int stages = room > 0 ? (int)(room / kStageBytes) : 0;
+        stages = stages < kMaxStages ? stages : kMaxStages;
+        if (stages >= 2 && encode_operand_sw128(&tma, A, M, K, kTileM) &&
+            encode_operand_sw128(&tmw, Wt, kTileN, K, kTileN)) {
+            const size_t smem = fixed + (size_t)stages * kStageBytes;
+            cudaError_t e = cudaFuncSetAttribute(tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int tiles = M / kTileM;
+            const int grid = tiles < sms ? tiles : sms;
+            tc_ws_kernel<<<grid, kWsThreads, smem, st>>>(tma, tmw, K, tiles, stages, bias, out, err);
+            ko_count_launch();
+            return cudaGetLastError();
+        }
+    }
+    // no room for two stages or no tensor-map encoder: the cp.async kernel
+    return launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
 }
 
 cudaError_t ko_mlp_layer_tc_t(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,

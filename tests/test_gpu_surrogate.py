@@ -164,6 +164,26 @@ def test_tcgen05_forward_matches_mma_and_oracle(ko):
     assert ms == oracle.makespan(s.gpu, s.kernels, order.tolist())
 
 
+def test_tcgen05_forward_many_tiles_bit_identical(ko):
+    """Rows for several 128-row tiles per CTA (ring stages and both TMEM
+    accumulators wrap) and a ragged last round: the tcgen05 layers give the
+    mma.sync path's bits exactly; sampled rows stay within the oracle's bar."""
+    p = _params(13)
+    B = 128 * (152 * 5 + 37)
+    x = _features(14, B)
+    m = ko.Model()
+    m.set_params(_flat(p))
+    m.set_tc(False)
+    y_mma = m.predict(x)
+    m.set_tc(True)
+    y_tc = m.predict(x)
+    m.close()
+    assert np.array_equal(y_tc.view(np.uint32), y_mma.view(np.uint32))
+    idx = np.linspace(0, B - 1, 512).astype(np.int64)
+    want, _ = mlp.forward(p, x[idx])
+    assert np.abs(y_tc[idx] - want).max() <= 2e-2 * max(1.0, np.abs(want).max())
+
+
 def test_chunk_size_does_not_change_results(ko):
     s = synth.gen_set("large", 3)
     m = ko.Model(seed=9)
