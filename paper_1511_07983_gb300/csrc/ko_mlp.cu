@@ -176,53 +176,147 @@ gemm_nt_kernel(const uint16_t *__restrict__ A, int lda, const uint16_t *__restri
 // x[b] = features of order rows[b] of set sid[b]: kernel at position p goes to
 // slot round(23 p / (N-1)); 7 features per slot; 8 global features; zeros
 // elsewhere.  Output bf16 row-major [B x 192] and transposed [192 x B].
-__global__ void encode_kernel(const int8_t *__restrict__ rows, int row_stride,
-                              const int *__restrict__ sid, const int *__restrict__ pick,
-                              const int *__restrict__ set_n, const float *__restrict__ kfeat,
-                              const float *__restrict__ gfeat, int B, uint16_t *x, uint16_t *xt)
+// Position of an N-kernel order whose slot is `slot`, or -1 (the slots of
+// distinct positions are distinct): slot(p) = (2*23*p + (n-1)) / (2(n-1)),
+// inverted by testing the positions nearest to slot*(n-1)/23.
+__device__ __forceinline__ int slot_position(int n, int slot)
 {
-    const int b = blockIdx.x;
-    if (b >= B) return;
-    const int src = pick ? pick[b] : b;
-    const int set = sid ? sid[src] : 0;
-    const int n = set_n[set];
-    const int8_t *row = rows + (size_t)src * row_stride;
-    for (int f = threadIdx.x; f < kMlpIn; f += blockDim.x) {
-        float v = 0.0f;
-        if (f < kSlots * kSlotFeat) {
-            const int slot = f / kSlotFeat, q = f % kSlotFeat;
-            // position whose slot is `slot` (slots of distinct positions are distinct)
-            int pos = -1;
-            if (n == 1) {
-                pos = slot == 0 ? 0 : -1;
+    if (n <= 1) return n == 1 && slot == 0 ? 0 : -1;
+    const int p0 = (slot * (n - 1)) / (kSlots - 1);
+    int pos = -1;
+    for (int p = p0 - 1; p <= p0 + 1; p++)
+        if (p >= 0 && p < n && (2 * (kSlots - 1) * p + (n - 1)) / (2 * (n - 1)) == slot) pos = p;
+    return pos;
+}
+
+// One thread per row, a warp per 32 consecutive rows.  Per block: the slot ->
+// position map of every N and -- for a single set (no sid) -- the set's
+// kernel and global features.  Per warp step: the 32 rows' order bytes are
+// copied to shared memory with coalesced loads (contiguous rows, no pick);
+// each thread produces its row's 192 features in order (slot by slot: one
+// kernel index, its 7 features; then the globals and the zero padding),
+// packs them two BF16 to a word (round to nearest even) and writes them to a
+// per-warp staging area (row pitch 400 bytes: conflict-free 16-byte stores);
+// the warp then stores its 32 rows (12,288 contiguous bytes) 16 bytes per
+// lane.  xt (training) gets the transposed copy value by value.
+constexpr int kEncWarps = 2, kEncPitch = 100;  // staging row pitch in words
+__global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const int8_t *__restrict__ rows, int row_stride,
+                                                                const int *__restrict__ sid,
+                                                                const int *__restrict__ pick,
+                                                                const int *__restrict__ set_n,
+                                                                const float *__restrict__ kfeat,
+                                                                const float *__restrict__ gfeat, int B,
+                                                                uint16_t *x, uint16_t *xt)
+{
+    __shared__ int8_t s_pos[kMaxK + 1][kSlots];
+    __shared__ float s_kf[kMaxK * kSlotFeat + kGlobals];
+    __shared__ __align__(16) int8_t s_rows[kEncWarps][32 * kMaxK];
+    __shared__ __align__(16) uint32_t s_out[kEncWarps][32 * kEncPitch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (kMaxK + 1) * kSlots; i += blockDim.x)
+        s_pos[i / kSlots][i % kSlots] = (int8_t)slot_position(i / kSlots, i % kSlots);
+    if (!sid) {
+        for (int i = threadIdx.x; i < kMaxK * kSlotFeat; i += blockDim.x) s_kf[i] = kfeat[i];
+        for (int i = threadIdx.x; i < kGlobals; i += blockDim.x) s_kf[kMaxK * kSlotFeat + i] = gfeat[i];
+    }
+    __syncthreads();
+    const bool stage = !pick && row_stride <= kMaxK;
+    const long long wsteps = ((long long)B + 31) / 32;
+    for (long long ws = (long long)blockIdx.x * kEncWarps + warp; ws < wsteps;
+         ws += (long long)gridDim.x * kEncWarps) {
+        const int base = (int)(ws * 32), nrows = B - base < 32 ? B - base : 32;
+        __syncwarp();  // the previous step's staging has been stored
+        if (stage) {
+            const int8_t *src = rows + (size_t)base * row_stride;
+            const int nb = nrows * row_stride;
+            if ((((uintptr_t)src) & 15u) == 0 && (nb & 15) == 0) {
+                // 16 bytes per lane: all loads in flight together
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+                uint4 *d4 = reinterpret_cast<uint4 *>(s_rows[warp]);
+                for (int i = lane; i < nb / 16; i += 32) d4[i] = s4[i];
             } else {
-                // invert slot = (2*23*p + (n-1)) / (2(n-1)): test the two nearest positions
-                const int p0 = (slot * (n - 1)) / (kSlots - 1);
-                for (int p = p0 - 1; p <= p0 + 1; p++) {
-                    if (p >= 0 && p < n && (2 * (kSlots - 1) * p + (n - 1)) / (2 * (n - 1)) == slot) pos = p;
-                }
+                for (int i = lane; i < nb; i += 32) s_rows[warp][i] = src[i];
             }
-            if (pos >= 0) v = kfeat[((size_t)set * kMaxK + row[pos]) * kSlotFeat + q];
-        } else if (f < kSlots * kSlotFeat + kGlobals) {
-            v = gfeat[set * kGlobals + (f - kSlots * kSlotFeat)];
+            __syncwarp();
         }
-        const uint16_t bits = bf16_bits(v);
-        x[(size_t)b * kMlpIn + f] = bits;
-        if (xt) xt[(size_t)f * B + b] = bits;
+        if (lane < nrows) {
+            const int b = base + lane;
+            const int src = pick ? pick[b] : b;
+            const int set = sid ? sid[src] : 0;
+            const int n = set_n[set];
+            const int8_t *row = stage ? &s_rows[warp][lane * row_stride] : rows + (size_t)src * row_stride;
+            const float *kf = sid ? kfeat + (size_t)set * kMaxK * kSlotFeat : s_kf;
+            const float *gf = sid ? gfeat + (size_t)set * kGlobals : s_kf + kMaxK * kSlotFeat;
+            uint32_t *out = &s_out[warp][lane * kEncPitch];
+            float v[8];
+            auto put = [&](int f, float val) {  // f is a constant after unrolling
+                v[f & 7] = val;
+                if ((f & 7) == 7) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; h++) {
+                        const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+                        memcpy(&w[h], &p2, sizeof(uint32_t));
+                    }
+                    *reinterpret_cast<uint4 *>(out + (f >> 3) * 4) = make_uint4(w[0], w[1], w[2], w[3]);
+                    if (xt) {
+#pragma unroll
+                        for (int h = 0; h < 8; h++)
+                            xt[(size_t)((f & ~7) + h) * B + b] = (uint16_t)(w[h >> 1] >> ((h & 1) * 16));
+                    }
+                }
+            };
+#pragma unroll
+            for (int slot = 0; slot < kSlots; slot++) {
+                const int pos = s_pos[n][slot];
+                const int k = pos >= 0 ? (int)row[pos] : -1;
+#pragma unroll
+                for (int q = 0; q < kSlotFeat; q++) put(slot * kSlotFeat + q, k >= 0 ? kf[k * kSlotFeat + q] : 0.0f);
+            }
+#pragma unroll
+            for (int g = 0; g < kGlobals; g++) put(kSlots * kSlotFeat + g, gf[g]);
+#pragma unroll
+            for (int f = kSlots * kSlotFeat + kGlobals; f < kMlpIn; f++) put(f, 0.0f);
+        }
+        __syncwarp();
+        // the warp's rows are contiguous in x: 16 bytes per lane per store
+        uint4 *dst = reinterpret_cast<uint4 *>(x + (size_t)base * kMlpIn);
+        for (int i = lane; i < nrows * (kMlpIn / 8); i += 32) {
+            const int r = i / (kMlpIn / 8), c = i % (kMlpIn / 8);
+            dst[i] = *reinterpret_cast<const uint4 *>(&s_out[warp][r * kEncPitch + c * 4]);
+        }
     }
 }
 
-// y[b] = A3[b] . w4 + b4 (one warp per row)
+// y[b] = A3[b] . w4 + b4: eight threads per row, thread c sums columns
+// 32c .. 32c + 31 as a chain of fused multiply-adds in column order, and the
+// eight partials combine as ((p0 + p1) + (p2 + p3)) + ((p4 + p5) + (p6 + p7))
+// before b4 is added (the order the fused tcgen05 last layer uses too).
 __global__ void out_fwd_kernel(const uint16_t *__restrict__ a3, const uint16_t *__restrict__ w4,
                                const float *__restrict__ b4, int B, float *y)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= B) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(i >> 3), c = (int)(i & 7);
     float s = 0.0f;
-    for (int k = lane; k < kHidden; k += 32)
-        s += bf16_val(a3[(size_t)warp * kHidden + k]) * bf16_val(w4[k]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[warp] = s + b4[0];
+    if (b < B) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a3 + (size_t)b * kHidden + c * 32);
+        const uint16_t *w = w4 + c * 32;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint4 v = src[q];
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                s = __fmaf_rn(__uint_as_float(u[h] << 16), bf16_val(w[8 * q + 2 * h]), s);
+                s = __fmaf_rn(__uint_as_float(u[h] & 0xFFFF0000u), bf16_val(w[8 * q + 2 * h + 1]), s);
+            }
+        }
+    }
+    // eight threads of a row sit in one aligned group of eight lanes
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (b < B && c == 0) y[b] = s + b4[0];
 }
 
 // Output layer backward: dy = 2 (y - t) / B; loss sum; dw4 = sum dy * A3; db4 = sum dy;
@@ -518,7 +612,13 @@ cudaError_t ko_mlp_encode(const int8_t *rows, int row_stride, const int *sid, co
                           const int *set_n, const float *kfeat, const float *gfeat, int B, uint16_t *x,
                           uint16_t *xt, cudaStream_t st)
 {
-    encode_kernel<<<B, 64, 0, st>>>(rows, row_stride, sid, pick, set_n, kfeat, gfeat, B, x, xt);
+    if (B <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks = ((long long)B + 32 * kEncWarps - 1) / (32 * kEncWarps);
+    const int grid = (int)(blocks < (long long)sms * 8 ? blocks : (long long)sms * 8);
+    encode_kernel<<<grid, kEncWarps * 32, 0, st>>>(rows, row_stride, sid, pick, set_n, kfeat, gfeat, B, x, xt);
     ko_count_launch();
     return cudaGetLastError();
 }
@@ -526,7 +626,7 @@ cudaError_t ko_mlp_encode(const int8_t *rows, int row_stride, const int *sid, co
 cudaError_t ko_mlp_out_fwd(const uint16_t *a3, const uint16_t *w4, const float *b4, int B, float *y,
                            cudaStream_t st)
 {
-    out_fwd_kernel<<<(B * 32 + 255) / 256, 256, 0, st>>>(a3, w4, b4, B, y);
+    out_fwd_kernel<<<(unsigned)(((long long)B * 8 + 255) / 256), 256, 0, st>>>(a3, w4, b4, B, y);
     ko_count_launch();
     return cudaGetLastError();
 }

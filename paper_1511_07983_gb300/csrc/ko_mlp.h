@@ -35,6 +35,14 @@ cudaError_t ko_mlp_gemm_relu(const uint16_t *A, int lda, const uint16_t *Bt, int
 // K in {192, 256}, N = 256; *err set to 1 if the MMA completion wait gave up.
 cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
                             int *err, cudaStream_t st);
+// tcgen05 last hidden layer fused with the output layer: y = a . w4 + b4 with
+// a = bf16(relu(A Wt^T + bias)) (not stored), in ko_mlp_out_fwd's summation
+// order, so y has the same bits as ko_mlp_layer_tc followed by
+// ko_mlp_out_fwd (which is what runs, through `out`, when the fused kernel
+// does not fit).  Same shapes as ko_mlp_layer_tc.
+cudaError_t ko_mlp_layer_tc_out(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias,
+                                const uint16_t *w4, const float *b4, uint16_t *out, float *y, int *err,
+                                cudaStream_t st);
 // tcgen05 training forward layer: also writes out_t = out transposed
 // ([256][ldt] BF16, ldt % 8 == 0).  Same shapes as ko_mlp_layer_tc.
 cudaError_t ko_mlp_layer_tc_t(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,

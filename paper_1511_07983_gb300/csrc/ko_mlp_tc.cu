@@ -379,10 +379,33 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar)
         saddr(mbar)));
 }
 
+// Barrier 1 across the epilogue warps, counting the threads whose `flag` is set.
+__device__ __forceinline__ int epi_barrier_count(bool flag)
+{
+    int n;
+    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %1, 0;\nbar.red.popc.u32 %0, 1, %2, p;\n}\n"
+                 : "=r"(n)
+                 : "r"((uint32_t)flag), "n"(kEpiWarps * 32)
+                 : "memory");
+    return n;
+}
+
+// OUT = false: out = bf16(relu(A Wt^T + bias)).  OUT = true (the network's
+// last hidden layer): the same BF16 activations are not stored but dotted
+// with w4 on the fly, y = a . w4 + b4, in a fixed order that
+// ko_mlp_out_fwd repeats: per row, eight 32-column partial sums, each a chain
+// of fused multiply-adds in column order, combined as
+// ((p0 + p1) + (p2 + p3)) + ((p4 + p5) + (p6 + p7)), then + b4.  Warp
+// (quarter, g) holds columns 64 g .. 64 g + 63 of 32 rows, i.e. p(2g) + p(2g+1);
+// the four such sums of a row meet in shared memory behind a named barrier
+// whose count also tells every epilogue warp whether all of them got the tile.
+template <bool OUT>
 __global__ void __launch_bounds__(kWsThreads, 1)
 tc_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int K, int tiles,
-             int stages, const float *__restrict__ bias, uint16_t *__restrict__ out, int *err)
+             int stages, const float *__restrict__ bias, uint16_t *__restrict__ out,
+             const uint16_t *__restrict__ w4, const float *__restrict__ b4, float *__restrict__ y, int *err)
 {
+    static_assert(!OUT || kEpiCols == 64, "the fused output sums assume 64 columns per epilogue warp");
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
     __shared__ __align__(8) uint64_t bar_acc[2], bar_free[2], bar_w, bar_drain;
@@ -419,6 +442,9 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
     for (int i = tid; i < kTileN; i += blockDim.x) sbias[i] = bias[i];
+    float *sw4 = sbias + kTileN;    // OUT: w4 as floats, then 2 x 4 x 128 partial sums
+    if (OUT)
+        for (int i = tid; i < kTileN; i += blockDim.x) sw4[i] = __uint_as_float((uint32_t)w4[i] << 16);
     tc_fence_sync();
     const uint32_t tmem = tmem_base;
 
@@ -503,39 +529,63 @@ tc_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         // epilogue: warps w, w + 4, ... share TMEM lanes 32 (w % 4).., kEpiCols columns each
         const int quarter = warp & 3, col0 = (warp >> 2) * kEpiCols;
         uint32_t *stage = (uint32_t *)(sbias + kTileN) + warp * 32 * kStageRowWords;
+        float *s_part = sw4 + kTileN;
+        const float b4v = OUT ? b4[0] : 0.0f;
         for (int i = 0; i < ntiles; i++) {
             const int b = i & 1;
             const bool got = ws_wait(&bar_acc[b], (uint32_t)(i >> 1) & 1u, &abort_flag, err);
-            if (!__all_sync(0xffffffffu, got)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const bool all = __all_sync(0xffffffffu, got);
+            if (!OUT && !all) break;
             const int row0 = ((int)blockIdx.x + i * (int)gridDim.x) * kTileM + quarter * 32;
             const uint32_t acc_t = tmem + (uint32_t)(b * kTileN);
-            for (int c0 = col0; c0 < col0 + kEpiCols; c0 += 32) {
-                uint32_t v[32];
-                tc_ld32(acc_t, quarter, c0, v);
-                uint32_t packed[16];
+            float part = 0.0f;
+            if (all) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                for (int c0 = col0; c0 < col0 + kEpiCols; c0 += 32) {
+                    uint32_t v[32];
+                    tc_ld32(acc_t, quarter, c0, v);
+                    uint32_t packed[16];
 #pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const float x0 = fmaxf(__uint_as_float(v[2 * q]) + sbias[c0 + 2 * q], 0.0f);
-                    const float x1 = fmaxf(__uint_as_float(v[2 * q + 1]) + sbias[c0 + 2 * q + 1], 0.0f);
-                    packed[q] = pack_bf16(x0, x1);
+                    for (int q = 0; q < 16; q++) {
+                        const float x0 = fmaxf(__uint_as_float(v[2 * q]) + sbias[c0 + 2 * q], 0.0f);
+                        const float x1 = fmaxf(__uint_as_float(v[2 * q + 1]) + sbias[c0 + 2 * q + 1], 0.0f);
+                        packed[q] = pack_bf16(x0, x1);
+                    }
+                    if constexpr (OUT) {
+                        // this row's 32-column partial: fused multiply-adds in column order
+                        float sum = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            sum = __fmaf_rn(__uint_as_float(packed[q] << 16), sw4[c0 + 2 * q], sum);
+                            sum = __fmaf_rn(__uint_as_float(packed[q] & 0xFFFF0000u), sw4[c0 + 2 * q + 1], sum);
+                        }
+                        part = c0 == col0 ? sum : part + sum;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            *(uint4 *)(stage + lane * 16 + ((q + (lane >> 1)) & 3) * 4) =
+                                make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int it = 0; it < 4; it++) {
+                            const int r = it * 8 + (lane >> 2), q = lane & 3;
+                            const uint4 w = *(const uint4 *)(stage + r * 16 + ((q + (r >> 1)) & 3) * 4);
+                            *(uint4 *)(out + (size_t)(row0 + r) * kTileN + c0 + q * 8) = w;
+                        }
+                        __syncwarp();
+                    }
                 }
-#pragma unroll
-                for (int q = 0; q < 4; q++)
-                    *(uint4 *)(stage + lane * 16 + ((q + (lane >> 1)) & 3) * 4) =
-                        make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
                 __syncwarp();
-#pragma unroll
-                for (int it = 0; it < 4; it++) {
-                    const int r = it * 8 + (lane >> 2), q = lane & 3;
-                    const uint4 w = *(const uint4 *)(stage + r * 16 + ((q + (r >> 1)) & 3) * 4);
-                    *(uint4 *)(out + (size_t)(row0 + r) * kTileN + c0 + q * 8) = w;
-                }
-                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_free[b]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_free[b]);
+            if constexpr (OUT) {
+                float *sp = s_part + b * 4 * kTileM + quarter * 32 + lane;
+                if (all) sp[(warp >> 2) * kTileM] = part;
+                // every epilogue warp arrives; the count says whether all of them got the tile
+                if (epi_barrier_count(all) != kEpiWarps * 32) break;
+                if ((warp >> 2) == 0) y[row0 + lane] = ((sp[0] + sp[kTileM]) + (sp[2 * kTileM] + sp[3 * kTileM])) + b4v;
+            }
         }
     }
     __syncthreads();
@@ -668,38 +718,58 @@ cudaError_t launch_layer(const uint16_t *A, const uint16_t *Wt, int M, int K, co
     return cudaGetLastError();
 }
 
+// Launch tc_ws_kernel<OUT> with as many 16 KB A stages as fit beside the
+// weights (1 KB kept for the static barriers); cudaErrorNotSupported when
+// fewer than two fit or no tensor-map encoder is available (the caller then
+// takes the cp.async path).
+template <bool OUT>
+cudaError_t launch_ws(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
+                      const uint16_t *w4, const float *b4, float *y, int *err, cudaStream_t st)
+{
+    CUtensorMap tma, tmw;
+    const size_t tail = OUT ? sizeof(float) * (kTileN + 2 * 4 * kTileM)
+                            : (size_t)kEpiWarps * 32 * kStageRowWords * sizeof(uint32_t);
+    const size_t fixed = (size_t)kTileN * K * 2 + sizeof(float) * kTileN + tail;
+    const long long room = (long long)max_dyn_smem() - 1024 - (long long)fixed;
+    int stages = room > 0 ? (int)(room / kStageBytes) : 0;
+    stages = stages < kMaxStages ? stages : kMaxStages;
+    if (stages < 2 || !encode_operand_sw128(&tma, A, M, K, kTileM) ||
+        !encode_operand_sw128(&tmw, Wt, kTileN, K, kTileN))
+        return cudaErrorNotSupported;
+    const size_t smem = fixed + (size_t)stages * kStageBytes;
+    cudaError_t e = cudaFuncSetAttribute(tc_ws_kernel<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = M / kTileM;
+    const int grid = tiles < sms ? tiles : sms;
+    tc_ws_kernel<OUT><<<grid, kWsThreads, smem, st>>>(tma, tmw, K, tiles, stages, bias, out, w4, b4, y, err);
+    ko_count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t ko_mlp_layer_tc(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,
                             int *err, cudaStream_t st)
 {
     if (M % kTileM || (K != 192 && K != 256)) return cudaErrorInvalidValue;
-    CUtensorMap tma, tmw;
-    {
-        // warp-specialised kernel: as many 16 KB A stages as fit beside the weights (1 KB kept
-        // for the static barriers)
-        const size_t fixed = (size_t)kTileN * K * 2 + sizeof(float) * kTileN +
-                             (size_t)kEpiWarps * 32 * kStageRowWords * sizeof(uint32_t);
-        const long long room = (long long)max_dyn_smem() - 1024 - (long long)fixed;
-        int stages = room > 0 ? (int)(room / kStageBytes) : 0;
-        stages = stages < kMaxStages ? stages : kMaxStages;
-        if (stages >= 2 && encode_operand_sw128(&tma, A, M, K, kTileM) &&
-            encode_operand_sw128(&tmw, Wt, kTileN, K, kTileN)) {
-            const size_t smem = fixed + (size_t)stages * kStageBytes;
-            cudaError_t e = cudaFuncSetAttribute(tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int tiles = M / kTileM;
-            const int grid = tiles < sms ? tiles : sms;
-            tc_ws_kernel<<<grid, kWsThreads, smem, st>>>(tma, tmw, K, tiles, stages, bias, out, err);
-            ko_count_launch();
-            return cudaGetLastError();
-        }
-    }
-    // no room for two stages or no tensor-map encoder: the cp.async kernel
+    const cudaError_t e = launch_ws<false>(A, Wt, M, K, bias, out, nullptr, nullptr, nullptr, err, st);
+    if (e != cudaErrorNotSupported) return e;
     return launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
+}
+
+cudaError_t ko_mlp_layer_tc_out(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias,
+                                const uint16_t *w4, const float *b4, uint16_t *out, float *y, int *err,
+                                cudaStream_t st)
+{
+    if (M % kTileM || (K != 192 && K != 256)) return cudaErrorInvalidValue;
+    const cudaError_t e = launch_ws<true>(A, Wt, M, K, bias, nullptr, w4, b4, y, err, st);
+    if (e != cudaErrorNotSupported) return e;
+    const cudaError_t e2 = launch_layer<0>(A, Wt, M, K, bias, out, nullptr, 0, nullptr, err, st);
+    if (e2 != cudaSuccess) return e2;
+    return ko_mlp_out_fwd(out, w4, b4, M, y, st);
 }
 
 cudaError_t ko_mlp_layer_tc_t(const uint16_t *A, const uint16_t *Wt, int M, int K, const float *bias, uint16_t *out,

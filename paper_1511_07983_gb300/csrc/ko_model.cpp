@@ -176,8 +176,9 @@ ko_status forward(ko_model *md, int B, bool train, cudaStream_t st)
     if (!train && md->tc_forward && B % 128 == 0) {
         if ((s = cuda_ok(ko_mlp_layer_tc(md->a0, md->w1t, B, kMlpIn, md->p + kOffB1, md->a1, md->tc_err, st)))) return s;
         if ((s = cuda_ok(ko_mlp_layer_tc(md->a1, md->w2t, B, kHidden, md->p + kOffB2, md->a2, md->tc_err, st)))) return s;
-        if ((s = cuda_ok(ko_mlp_layer_tc(md->a2, md->w3t, B, kHidden, md->p + kOffB3, md->a3, md->tc_err, st)))) return s;
-        return cuda_ok(ko_mlp_out_fwd(md->a3, md->w4b, md->p + kOffB4, B, md->y, st));
+        // the last hidden layer and the output layer in one kernel: a3 is not written
+        return cuda_ok(ko_mlp_layer_tc_out(md->a2, md->w3t, B, kHidden, md->p + kOffB3, md->w4b, md->p + kOffB4,
+                                           md->a3, md->y, md->tc_err, st));
     }
     if ((s = cuda_ok(ko_mlp_gemm_relu(md->a0, kMlpIn, md->w1t, kMlpIn, B, kHidden, kMlpIn, md->p + kOffB1,
                                       md->a1, kHidden, train ? md->a1t : nullptr, B, st))))
