@@ -13,10 +13,12 @@
 //                          split-K, one 256-wide K slice per CTA, FP32 partial
 //                          tiles to a workspace; wgrad_reduce_kernel sums the
 //                          slices in a fixed order (deterministic).
-//   tc_ws_kernel           the MODE 0 layer, warp-specialised: TMA producer,
+//   tc_ws_kernel<OUT>      the MODE 0 layer, warp-specialised: TMA producer,
 //                          MMA issuer and epilogue warps over a ring of
 //                          128-byte-swizzled A stages and two TMEM
-//                          accumulators (the default for inference).
+//                          accumulators (the default for inference); with
+//                          OUT the network's output layer is fused into the
+//                          last hidden layer's epilogue.
 //
 //  * The cp.async kernels keep operands in the no-swizzle core-matrix layout: a
 //    core matrix is 8 rows x 16 bytes; core matrices adjacent along K are
