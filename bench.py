@@ -283,7 +283,7 @@ def run_ours(a):
     elif a.autotune:
         t0 = time.perf_counter()
         choice = g.autotune(os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"))
-        tune = {"lanes": choice["lanes"], "levels": choice["levels"],
+        tune = {"lanes": choice["lanes"], "levels": choice["levels"], "lane_state": choice["lane_state"],
                 "seconds": round(time.perf_counter() - t0, 2)}
     stream = torch.cuda.current_stream()
     d_hist = torch.zeros(NBINS, dtype=torch.int64, device="cuda")   # uint64 bits
@@ -371,7 +371,8 @@ def run_ours(a):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MB flush before every step; the 3.8 GB makespan buffer exceeds L2",
                    "lanes": ko.ko_get_option(g.h, ko.KO_OPT_LANES),
-                   "levels": ko.ko_get_option(g.h, ko.KO_OPT_LEVELS), "autotune": tune},
+                   "levels": ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
+                   "lane_state": ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE), "autotune": tune},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": kernel, "kernel_ms": kernel_s * 1e3,
@@ -530,9 +531,10 @@ def run_batch(a):
         t0 = time.perf_counter()
         ko.ko_batch_autotune(gpus, os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"))
         choices = sorted({(ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
-                           ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL)) for g in gpus})
+                           ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL), ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE))
+                          for g in gpus})
         tune = {"seconds": round(time.perf_counter() - t0, 2),
-                "choices (lanes, levels, global slab)": [list(c) for c in choices]}
+                "choices (lanes, levels, global slab, lane state)": [list(c) for c in choices]}
     t0 = time.perf_counter()
     b = ko.Batch(gpus, nbins=nbins)
     build_s = time.perf_counter() - t0

@@ -210,6 +210,12 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
  *                       hold before its work item moves to the simple
  *                       simulator, 1..32 (default 32; small values exercise
  *                       that hand-over)
+ *   KO_OPT_LANE_STATE   state size of the one-thread-per-order simulator
+ *                       (KO_OPT_LANES = 1): 0 = 14 runs and 56 group slots
+ *                       (288 simulations per SM, default), 1 = 12 runs and
+ *                       40 slots (352), 2 = 10 runs and 32 slots (448).
+ *                       Smaller states fit more simulations on an SM; work
+ *                       items that need more move on to the run-length passes
  * Results never depend on these knobs.  KO_ERR_ARG for an unknown key or
  * value. */
 #define KO_OPT_LANES 1
@@ -217,6 +223,7 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
 #define KO_OPT_SIMPLE_ONLY 3
 #define KO_OPT_RUN_LIMIT 4
 #define KO_OPT_STACK_GLOBAL 5
+#define KO_OPT_LANE_STATE 6
 ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value);
 
 /* Current value of a tuning knob (KO_OPT_*), or KO_ERR_ARG. */
@@ -225,9 +232,11 @@ int64_t ko_get_option(const ko_gpu *g, int32_t key);
 /* Autotuner: times the exhaustive simulators on a calibration slice of this
  * set's exhaustive space (the whole space up to 64M orders, else 64M orders in
  * 16 evenly spread ranges) for every candidate -- 1, 16 or 32 threads per
- * simulation; for 16 and 32, saved DFS node states in a global slab or in
- * shared memory; 1..min(N-1, 5) saved DFS levels -- keeps the fastest and sets
- * KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL on the handle.  With
+ * simulation; for 1, the three state sizes of KO_OPT_LANE_STATE; for 16 and
+ * 32, saved DFS node states in a global slab or in shared memory;
+ * 1..min(N-1, 5) saved DFS levels -- keeps the fastest and sets
+ * KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL / KO_OPT_LANE_STATE on
+ * the handle.  With
  * cache_path (nullable) the choice is looked up first and stored after, keyed
  * by (N_SM class, N), in a small JSON file.  Synchronises `stream`; results
  * never depend on the choice.  N <= 12. */
@@ -239,7 +248,8 @@ ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream);
  * orders) together as one exhaustive launch per candidate (the candidates of
  * ko_autotune) and keeps the fastest, so small sets are timed as a batch runs
  * them; smaller classes keep 16 lanes, a global slab and min(N-1, 4) levels.
- * Sets every handle's KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL.  With
+ * Sets every handle's KO_OPT_LANES / KO_OPT_LEVELS / KO_OPT_STACK_GLOBAL /
+ * KO_OPT_LANE_STATE.  With
  * cache_path (nullable) each class's choice is looked up first and stored
  * after (keys "B_S<class>_N<n>").  KO_ERR_TOO_LARGE for N > 12,
  * KO_ERR_OVERFLOW for a set whose durations reach 2^31 cycles.  Synchronises
@@ -273,9 +283,10 @@ ko_status ko_transfer_bytes(const ko_gpu *g, int64_t *h2d, int64_t *d2h);
  * evaluation of Sec. 6 repeated over a population of kernel sets).
  *
  * ko_batch_create snapshots nsets handles (kernels, limits, capacities, each
- * handle's KO_OPT_LEVELS, KO_OPT_LANES and KO_OPT_STACK_GLOBAL -- sets that
- * share lanes and node-state placement run in one launch, one launch per
- * such group -- and KO_OPT_RUN_LIMIT of the first handle), computes
+ * handle's KO_OPT_LEVELS, KO_OPT_LANES, KO_OPT_STACK_GLOBAL and
+ * KO_OPT_LANE_STATE -- sets that share lanes, node-state placement and state
+ * size run in one launch, one launch per such group -- and KO_OPT_RUN_LIMIT
+ * of the first handle), computes
  * each set's Algorithm 1 order on the host, lays out one work list over all
  * sets (largest sets first) and captures the whole evaluation -- reset,
  * ranked-order makespans, all N! orders of every set, optional per-set

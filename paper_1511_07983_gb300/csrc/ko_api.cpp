@@ -623,6 +623,10 @@ ko_status ko_set_option(ko_gpu *g, int32_t key, int64_t value)
         if (value != 0 && value != 1) return fail(KO_ERR_ARG);
         g->fast.stack_global = (int)value;
         break;
+    case KO_OPT_LANE_STATE:
+        if (value < 0 || value > 2) return fail(KO_ERR_ARG);
+        g->fast.lane_shape = (int)value;
+        break;
     default:
         return fail(KO_ERR_ARG);
     }
@@ -638,6 +642,7 @@ int64_t ko_get_option(const ko_gpu *g, int32_t key)
     case KO_OPT_SIMPLE_ONLY: return g->fast.disabled ? 1 : 0;
     case KO_OPT_RUN_LIMIT: return g->fast.run_limit;
     case KO_OPT_STACK_GLOBAL: return g->fast.stack_global;
+    case KO_OPT_LANE_STATE: return g->fast.lane_shape;
     default: return fail(KO_ERR_ARG);
     }
 }
@@ -652,13 +657,14 @@ ko_status ko_autotune(ko_gpu *g, const char *cache_path, void *stream)
     ko_status s = prepare(g, st);
     if (s) return fail(s);
     if ((s = upload_meta(g, st))) return fail(s);
-    int lanes = 16, levels = 4, stack = 1;
+    int lanes = 16, levels = 4, stack = 1, shape = 0;
     double rate = 0.0;
-    s = ko_tune_set(&g->fast, g->h, g->d_set, g->d_acc, cache_path, st, &lanes, &levels, &stack, &rate);
+    s = ko_tune_set(&g->fast, g->h, g->d_set, g->d_acc, cache_path, st, &lanes, &levels, &stack, &shape, &rate);
     if (s) return fail(s);
     g->fast.lanes = lanes;
     g->fast.levels = levels;
     g->fast.stack_global = stack;
+    g->fast.lane_shape = shape;
     return ok();
 }
 
@@ -672,14 +678,15 @@ ko_status ko_batch_autotune(ko_gpu *const *sets, int32_t nsets, const char *cach
         if (!ko_fast_applicable(sets[i]->h)) return fail(KO_ERR_OVERFLOW);
         hs[i] = &sets[i]->h;
     }
-    std::vector<int> lanes(nsets), levels(nsets), stack(nsets);
+    std::vector<int> lanes(nsets), levels(nsets), stack(nsets), shape(nsets);
     ko_status s = ko_tune_batch(hs.data(), nsets, cache_path, (cudaStream_t)stream, lanes.data(), levels.data(),
-                                stack.data());
+                                stack.data(), shape.data());
     if (s) return fail(s);
     for (int i = 0; i < nsets; i++) {
         sets[i]->fast.lanes = lanes[i];
         sets[i]->fast.levels = levels[i];
         sets[i]->fast.stack_global = stack[i];
+        sets[i]->fast.lane_shape = shape[i];
     }
     return ok();
 }
@@ -703,7 +710,7 @@ ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
         return nullptr;
     }
     std::vector<const KoSet *> hs(nsets);
-    std::vector<int> levels(nsets), lanes(nsets), stack(nsets);
+    std::vector<int> levels(nsets), lanes(nsets), stack(nsets), shape(nsets);
     for (int i = 0; i < nsets; i++) {
         if (!sets[i] || sets[i]->h.sampling != KO_SAMPLE_BURST_END) {
             fail(KO_ERR_ARG);
@@ -714,9 +721,10 @@ ko_batch *ko_batch_create(ko_gpu *const *sets, int32_t nsets, int32_t nbins)
         levels[i] = sets[i]->fast.levels;
         lanes[i] = sets[i]->fast.lanes;
         stack[i] = sets[i]->fast.stack_global;
+        shape[i] = sets[i]->fast.lane_shape;
     }
     ko_status err = KO_OK;
-    ko_batch *b = ko_batch_build(hs.data(), levels.data(), lanes.data(), stack.data(), nsets, nbins,
+    ko_batch *b = ko_batch_build(hs.data(), levels.data(), lanes.data(), stack.data(), shape.data(), nsets, nbins,
                                  sets[0]->fast.run_limit, &err);
     if (!b) fail(err);
     else ok();

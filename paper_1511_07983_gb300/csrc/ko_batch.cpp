@@ -42,7 +42,7 @@ struct ko_batch {
     long long *h_refs = nullptr;      // pinned
     int levels_max = 1;
     struct Group {
-        int lanes, stack;
+        int lanes, stack, shape;  // shape: the one-thread pass's state size
         int chunk0, nchunks;      // into the exhaustive chunks
         long long n_items;
         int levels;               // deepest saved levels of its sets
@@ -113,6 +113,7 @@ ko_status enqueue(ko_batch *b, cudaStream_t st)
         x.levels = gr.levels;
         b->fast.lanes = gr.lanes;
         b->fast.stack_global = gr.stack;
+        b->fast.lane_shape = gr.shape;
         if ((s = ko_fast_launch(&b->fast, x, b->slab, st))) return s;
     }
     if (b->nbins > 0) {
@@ -136,7 +137,7 @@ ko_status enqueue(ko_batch *b, cudaStream_t st)
 }  // namespace
 
 ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int *lanes, const int *stack,
-                         int nsets, int nbins, int run_limit, ko_status *err)
+                         const int *shape, int nsets, int nbins, int run_limit, ko_status *err)
 {
     *err = KO_OK;
     if (nsets < 1 || nbins < 0 || nbins > 32768) { *err = KO_ERR_ARG; return nullptr; }
@@ -173,7 +174,7 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int 
     // exhaustive chunks: grouped by simulator choice, most expensive set first in each group
     std::vector<int> idx(nsets);
     std::iota(idx.begin(), idx.end(), 0);
-    auto gkey = [&](int i) { return lanes[i] * 2 + (stack[i] ? 1 : 0); };
+    auto gkey = [&](int i) { return lanes[i] * 8 + shape[i] * 2 + (stack[i] ? 1 : 0); };
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
         if (gkey(x) != gkey(y)) return gkey(x) < gkey(y);
         return kFact[b->h_sets[x].n] * order_cost(b->h_sets[x]) > kFact[b->h_sets[y].n] * order_cost(b->h_sets[y]);
@@ -189,7 +190,7 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int 
     for (int k = 0; k < nsets; k++) {
         const int i = idx[k];
         if (k == 0 || gkey(i) != gkey(idx[k - 1])) {
-            b->groups.push_back(ko_batch::Group{lanes[i], stack[i] ? 1 : 0, k, 0, 0, 1});
+            b->groups.push_back(ko_batch::Group{lanes[i], stack[i] ? 1 : 0, shape[i], k, 0, 0, 1});
             first = 0;  // each group is its own launch, items counted from 0
         }
         ko_batch::Group &gr = b->groups.back();
@@ -249,6 +250,7 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int 
         none.reserve_items = longest;
         b->fast.lanes = gr.lanes;
         b->fast.stack_global = gr.stack;
+        b->fast.lane_shape = gr.shape;
         if (ko_fast_launch(&b->fast, none, b->slab, b->cap_stream) != KO_OK ||
             cudaStreamSynchronize(b->cap_stream) != cudaSuccess) {
             cudaGetLastError();

@@ -910,7 +910,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
     const bool lane = fs->lanes == 1;
     if (lane) {
         // one-thread-per-order pass: a node-state slab for every thread it runs
-        const size_t need = ko_lane_slab_bytes(w.levels < 1 ? 1 : w.levels);
+        const size_t need = ko_lane_slab_bytes(w.levels < 1 ? 1 : w.levels, fs->lane_shape);
         if (fs->lslab_bytes < need) {
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -970,7 +970,7 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
         w0.ov_list = fb->ov_list;
         w0.gstack = (int *)fs->lslab;
         w0.gstack_words = (long long)(fs->lslab_bytes / sizeof(int));
-        if ((e = ko_launch_lane(w0, st)) != cudaSuccess) {
+        if ((e = ko_launch_lane(w0, fs->lane_shape, st)) != cudaSuccess) {
             cudaGetLastError();
             return KO_ERR_CUDA;
         }

@@ -58,6 +58,7 @@ struct KoFastState {
     bool disabled = false;      // use the simple simulator only
     int run_limit = 32;         // cap on runs per simulation (tests force the hand-over)
     int stack_global = 1;       // DFS node states in global memory (1) or shared memory (0)
+    int lane_shape = 0;         // one-thread pass state: 0 = 14 runs / 56 group slots, 1 = 12 / 40, 2 = 10 / 32
     void *gstack = nullptr;     // global slab for node states
     size_t gstack_bytes = 0;
     void *lslab = nullptr;      // node-state slab of the one-thread-per-order pass
@@ -84,9 +85,9 @@ ko_status ko_fast_launch(KoFastState *fs, KoWork w, size_t max_slab_bytes, cudaS
 
 // One-thread-per-order pass (ko_lane.cu) over the items of `w` (counters and
 // the abandoned-item list already set; w.gstack = its node-state slab of
-// ko_lane_slab_bytes(w.levels) bytes).
-cudaError_t ko_launch_lane(const KoWork &w, cudaStream_t st);
-size_t ko_lane_slab_bytes(int levels);
+// ko_lane_slab_bytes(w.levels, shape) bytes); shape as KoFastState::lane_shape.
+cudaError_t ko_launch_lane(const KoWork &w, int shape, cudaStream_t st);
+size_t ko_lane_slab_bytes(int levels, int shape);
 
 // Device address of the count of items the first pass of the last launch
 // abandoned (followed by the count the wide second pass abandoned).

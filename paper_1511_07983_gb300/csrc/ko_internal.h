@@ -76,7 +76,7 @@ cudaError_t ko_launch_accum_reset(KoAccum *acc, int count, cudaStream_t stream);
 
 // Batch internals (ko_batch.cpp).
 ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int *lanes, const int *stack,
-                         int nsets, int nbins, int run_limit, ko_status *err);
+                         const int *shape, int nsets, int nbins, int run_limit, ko_status *err);
 ko_status ko_batch_exec(ko_batch *b, ko_rank *out, uint64_t *hist, bool hist_dev, cudaStream_t st);
 long long ko_batch_orders_impl(const ko_batch *b);
 unsigned long long ko_batch_fallback(const ko_batch *b);
@@ -87,9 +87,9 @@ struct KoFastState;
 struct KoChunk;
 ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAccum *d_acc,
                       const char *cache_path, cudaStream_t st, int *lanes_out, int *levels_out,
-                      int *stack_out, double *rate_out);
+                      int *stack_out, int *shape_out, double *rate_out);
 ko_status ko_tune_batch(const KoSet *const *hs, int nsets, const char *cache_path, cudaStream_t st,
-                        int *lanes_out, int *levels_out, int *stack_out);
+                        int *lanes_out, int *levels_out, int *stack_out, int *shape_out);
 
 // Surrogate model internals (ko_model.cpp).
 ko_model *ko_model_new(uint64_t seed, ko_status *err);

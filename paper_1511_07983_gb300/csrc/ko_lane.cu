@@ -23,11 +23,15 @@ namespace {
 using namespace kolane;
 
 constexpr unsigned kAll = 0xffffffffu;
-#ifndef KO_LANE_THREADS
-#define KO_LANE_THREADS 288
-#endif
-constexpr int kLaneThreads = KO_LANE_THREADS;   // one block per SM: this many columns of kWords words
-static_assert(kLaneThreads % 32 == 0 && kLaneThreads * kWords * 4 <= 232448, "one block's columns fit an SM");
+// One block per SM: as many simulations (columns of SH::kWords words) as fit
+// its shared memory, in whole warps.
+template <class SH>
+constexpr int lane_threads()
+{
+    return (232448 / (SH::kWords * 4)) / 32 * 32;
+}
+static_assert(lane_threads<ShapeL>() == 288 && lane_threads<ShapeM>() == 352 && lane_threads<ShapeS>() == 448,
+              "simulations per SM of the three shapes");
 // Threads of a warp that must wait for the control step before it runs.
 #ifndef KO_LANE_GATHER
 #define KO_LANE_GATHER 16
@@ -77,11 +81,12 @@ __device__ __forceinline__ int nth_unused(uint32_t used, uint32_t all, unsigned 
 
 enum Phase : int { PH_FETCH = 0, PH_NEXT, PH_START, PH_EVENT, PH_FINAL, PH_PLACED, PH_DONE };
 
-template <int T>
+template <int T, class SH>
 __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
 {
+    constexpr int kRuns = SH::kRuns, kWords = SH::kWords, kSaveWords = SH::kSaveWords;
     extern __shared__ uint32_t lane_cols[];
-    LaneSim<T, GKern> sim;
+    LaneSim<T, GKern, SH> sim;
     sim.col = lane_cols + threadIdx.x;
     sim.run_limit = a.run_limit < kRuns ? a.run_limit : kRuns;
 
@@ -308,34 +313,52 @@ __global__ void __launch_bounds__(T, 1) lane_kernel(KoWork a)
 
 }  // namespace
 
-size_t ko_lane_slab_bytes(int levels)
+namespace {
+
+template <class SH>
+size_t slab_bytes(int levels)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (levels < 1) levels = 1;
-    return sizeof(uint32_t) * (size_t)sms * kLaneThreads * levels * kSaveWords;
+    return sizeof(uint32_t) * (size_t)sms * lane_threads<SH>() * levels * SH::kSaveWords;
 }
 
-cudaError_t ko_launch_lane(const KoWork &a, cudaStream_t st)
+template <class SH>
+cudaError_t launch_lane(const KoWork &a, cudaStream_t st)
 {
-    const size_t smem = sizeof(uint32_t) * (size_t)kWords * kLaneThreads;
-    cudaError_t e = cudaFuncSetAttribute(lane_kernel<kLaneThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    constexpr int T = lane_threads<SH>();
+    const size_t smem = sizeof(uint32_t) * (size_t)SH::kWords * T;
+    cudaError_t e = cudaFuncSetAttribute(lane_kernel<T, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int levels = a.levels < 1 ? 1 : a.levels;
     long long blocks = sms;
-    const long long fit = a.gstack_words / ((long long)kLaneThreads * levels * kSaveWords);
+    const long long fit = a.gstack_words / ((long long)T * levels * SH::kSaveWords);
     if (blocks > fit) blocks = fit;
     if (blocks < 1) return cudaErrorInvalidValue;  // the slab holds no thread's node states
     const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
-    const long long needed = (work + kLaneThreads - 1) / kLaneThreads;
+    const long long needed = (work + T - 1) / T;
     if (blocks > needed) blocks = needed;
     if (blocks < 1) blocks = 1;  // an empty list (a sizing launch): one block finds no work
-    lane_kernel<kLaneThreads><<<(unsigned)blocks, kLaneThreads, smem, st>>>(a);
+    lane_kernel<T, SH><<<(unsigned)blocks, T, smem, st>>>(a);
     ko_count_launch();
     return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ko_lane_slab_bytes(int levels, int shape)
+{
+    return shape == 2 ? slab_bytes<ShapeS>(levels) : shape == 1 ? slab_bytes<ShapeM>(levels)
+                                                                : slab_bytes<ShapeL>(levels);
+}
+
+cudaError_t ko_launch_lane(const KoWork &a, int shape, cudaStream_t st)
+{
+    return shape == 2 ? launch_lane<ShapeS>(a, st) : shape == 1 ? launch_lane<ShapeM>(a, st)
+                                                                : launch_lane<ShapeL>(a, st);
 }

@@ -49,39 +49,42 @@
 
 namespace kolane {
 
-#ifndef KO_LANE_RUNS
-#define KO_LANE_RUNS 14
-#endif
-#ifndef KO_LANE_POOL
-#define KO_LANE_POOL 56
-#endif
-constexpr int kRuns = KO_LANE_RUNS;   // runs one simulation may hold (at most 16)
-constexpr int kPool = KO_LANE_POOL;   // group slots of one simulation (even, at most 64)
-static_assert(kRuns <= 16 && kPool <= 64 && kPool % 2 == 0, "run and slot masks are 32 and 64 bits");
-constexpr unsigned long long kPoolAll = kPool == 64 ? ~0ull : ((1ull << kPool) - 1ull);
-
-enum : int {
-    W_RB = 0,                      // run: first SM | SM count << 16
-    W_RU = W_RB + kRuns,           // run: registers | blocks << 19 | warps << 25 in use per SM
-    W_RS = W_RU + kRuns,           // run: shared memory in use per SM
-    W_RC = W_RS + kRuns,           // run: SumC
-    W_RM = W_RC + kRuns,           // run: SumM
-    W_RE = W_RM + kRuns,           // run: earliest end of its started groups (where valid)
-    W_RG0 = W_RE + kRuns,          // run: pool slots 0..31 it holds
-    W_RG1 = W_RG0 + kRuns,         // run: pool slots 32..63
-    W_GE = W_RG1 + kRuns,          // slot: end (mod 2^32)
-    W_GD = W_GE + kPool,           // slots 2w, 2w+1: 16-bit descriptors
-    kWords = W_GD + kPool / 2      // 200 with 14 runs and 56 slots
+// State shape of one simulation: RUNS runs and POOL group slots, laid out as
+// the column words below.  Smaller shapes let more simulations share an SM's
+// shared memory; a work item that needs more is handed on (see LaneSim).
+template <int RUNS, int POOL>
+struct Shape {
+    static_assert(RUNS <= 16 && POOL <= 64 && POOL % 2 == 0, "run and slot masks are 32 and 64 bits");
+    static constexpr int kRuns = RUNS;   // runs one simulation may hold
+    static constexpr int kPool = POOL;   // group slots of one simulation
+    static constexpr unsigned long long kPoolAll = POOL == 64 ? ~0ull : ((1ull << POOL) - 1ull);
+    static constexpr int W_RB = 0;                 // run: first SM | SM count << 16
+    static constexpr int W_RU = W_RB + RUNS;       // run: registers | blocks << 19 | warps << 25 in use per SM
+    static constexpr int W_RS = W_RU + RUNS;       // run: shared memory in use per SM
+    static constexpr int W_RC = W_RS + RUNS;       // run: SumC
+    static constexpr int W_RM = W_RC + RUNS;       // run: SumM
+    static constexpr int W_RE = W_RM + RUNS;       // run: earliest end of its started groups (where valid)
+    static constexpr int W_RG0 = W_RE + RUNS;      // run: pool slots 0..31 it holds
+    static constexpr int W_RG1 = W_RG0 + RUNS;     // run: pool slots 32..63
+    static constexpr int W_GE = W_RG1 + RUNS;      // slot: end (mod 2^32)
+    static constexpr int W_GD = W_GE + POOL;       // slots 2w, 2w+1: 16-bit descriptors
+    static constexpr int kWords = W_GD + POOL / 2; // 8 words per run, 1.5 per slot
+    static constexpr int kSaveWords = kWords + 12; // with the registers of a node state
+    static_assert(kWords % 4 == 0, "node states are copied in 16-byte pieces");
 };
+// The shapes the one-thread simulator is built for: 14 runs / 56 slots (200
+// words), 12 / 40 (156 words), 10 / 32 (128 words).
+using ShapeL = Shape<14, 56>;
+using ShapeM = Shape<12, 40>;
+using ShapeS = Shape<10, 32>;
+
 // Descriptor: kernel (bits 0-4) | blocks per SM - 1 (bits 5-10) | owner run (bits 11-14).
 constexpr uint32_t kDescKernel = 31u, kDescOwnerShift = 11;
 // Packed usage word: registers in bits 0-18, blocks 19-24, warps 25-31.
 constexpr uint32_t kRegMask = (1u << 19) - 1u;
 
-// Registers saved with a node state (beside the kWords column words).
+// Registers saved with a node state (beside the column words).
 constexpr int kRegWords = 12;
-constexpr int kSaveWords = kWords + kRegWords;   // 212 = 53 x 16 bytes with 14 runs and 56 slots
-static_assert(kWords % 4 == 0, "node states are copied in 16-byte pieces");
 
 // The set's limits, per thread.
 struct Limits {
@@ -155,8 +158,12 @@ struct KRel {
     uint32_t s, c, m;
 };
 
-template <int STRIDE, class KLoad>
+template <int STRIDE, class KLoad, class SH>
 struct LaneSim {
+    static constexpr int kRuns = SH::kRuns, kPool = SH::kPool, kWords = SH::kWords;
+    static constexpr unsigned long long kPoolAll = SH::kPoolAll;
+    static constexpr int W_RB = SH::W_RB, W_RU = SH::W_RU, W_RS = SH::W_RS, W_RC = SH::W_RC, W_RM = SH::W_RM,
+                         W_RE = SH::W_RE, W_RG0 = SH::W_RG0, W_RG1 = SH::W_RG1, W_GE = SH::W_GE, W_GD = SH::W_GD;
     uint32_t *col;            // word f at col[f * STRIDE]
     KLoad kl;                 // kernel constants by id
     Limits L;

@@ -28,7 +28,7 @@
 namespace {
 
 struct Choice {
-    int lanes = 16, levels = 4, stack = 1;
+    int lanes = 16, levels = 4, stack = 1, shape = 0;  // shape: the one-thread pass's state size
     double rate = 0.0;
 };
 
@@ -69,18 +69,22 @@ std::map<std::string, Choice> read_cache(const char *path)
         }
         const std::string body = text.substr(q1, close - q1);
         Choice c;
-        int lanes = 0, levels = -1, stack = 1;
+        int lanes = 0, levels = -1, stack = 1, shape = 0;
         double rate = 0.0;
         const size_t pl = body.find("\"lanes\":"), pv = body.find("\"levels\":"),
-                     pr = body.find("\"orders_per_s\":"), ps = body.find("\"stack\":");
+                     pr = body.find("\"orders_per_s\":"), ps = body.find("\"stack\":"),
+                     ph = body.find("\"shape\":");
         if (pl != std::string::npos) lanes = std::atoi(body.c_str() + pl + 8);
         if (pv != std::string::npos) levels = std::atoi(body.c_str() + pv + 9);
         if (pr != std::string::npos) rate = std::atof(body.c_str() + pr + 15);
         if (ps != std::string::npos) stack = std::atoi(body.c_str() + ps + 8);
-        if ((lanes == 1 || lanes == 16 || lanes == 32) && levels >= 0 && levels <= 6 && (stack == 0 || stack == 1)) {
+        if (ph != std::string::npos) shape = std::atoi(body.c_str() + ph + 8);
+        if ((lanes == 1 || lanes == 16 || lanes == 32) && levels >= 0 && levels <= 6 && (stack == 0 || stack == 1) &&
+            shape >= 0 && shape <= 2) {
             c.lanes = lanes;
             c.levels = levels;
             c.stack = stack;
+            c.shape = shape;
             c.rate = rate;
             m[key] = c;
         }
@@ -98,9 +102,10 @@ void write_cache(const char *path, const std::map<std::string, Choice> &m)
     std::fprintf(f, "{\n");
     size_t i = 0;
     for (const auto &kv : m) {
-        std::fprintf(f, "  \"%s\": {\"lanes\": %d, \"levels\": %d, \"stack\": %d, \"orders_per_s\": %.6g}%s\n",
-                     kv.first.c_str(), kv.second.lanes, kv.second.levels, kv.second.stack, kv.second.rate,
-                     ++i < m.size() ? "," : "");
+        std::fprintf(f,
+                     "  \"%s\": {\"lanes\": %d, \"levels\": %d, \"stack\": %d, \"shape\": %d, \"orders_per_s\": %.6g}%s\n",
+                     kv.first.c_str(), kv.second.lanes, kv.second.levels, kv.second.stack, kv.second.shape,
+                     kv.second.rate, ++i < m.size() ? "," : "");
     }
     std::fprintf(f, "}\n");
     std::fclose(f);
@@ -149,11 +154,12 @@ long long ko_tune_chunks(int n, int d0, std::vector<KoChunk> &out)
 // Times one launch over `w` with the candidate's lanes and node-state
 // placement (best of `reps`); returns orders per second (0 on failure).
 static double time_candidate(KoFastState *fs, const KoWork &w, KoAccum *d_acc, int nacc, long long orders,
-                             int lanes, int stack, size_t slab, int reps, cudaStream_t st)
+                             int lanes, int stack, int shape, size_t slab, int reps, cudaStream_t st)
 {
-    const int saved_lanes = fs->lanes, saved_stack = fs->stack_global;
+    const int saved_lanes = fs->lanes, saved_stack = fs->stack_global, saved_shape = fs->lane_shape;
     fs->lanes = lanes;
     fs->stack_global = stack;
+    fs->lane_shape = shape;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double rate = 0.0;
     if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
@@ -173,20 +179,23 @@ static double time_candidate(KoFastState *fs, const KoWork &w, KoAccum *d_acc, i
     cudaGetLastError();
     fs->lanes = saved_lanes;
     fs->stack_global = saved_stack;
+    fs->lane_shape = saved_shape;
     return rate;
 }
 
-// The candidates: one thread per order (its node states always in the global
-// slab), or 16 / 32 lanes with node states in the global slab or in shared
-// memory; 1 .. min(N - 1, 5) saved levels each.
+// The candidates: one thread per order (node states always in the global
+// slab) with each of the three state shapes (14 runs / 56 group slots at 288
+// simulations per SM, 12 / 40 at 352, 10 / 32 at 448), or 16 / 32 lanes with
+// node states in the global slab or in shared memory; 1 .. min(N - 1, 5)
+// saved levels each.
 static std::vector<Choice> candidates(int n)
 {
     std::vector<Choice> c;
     const int max_levels = n - 1 < 5 ? n - 1 : 5;
     for (int levels = 1; levels <= (max_levels > 1 ? max_levels : 1); levels++) {
-        c.push_back(Choice{1, levels, 1, 0.0});
+        for (int shape : {0, 1, 2}) c.push_back(Choice{1, levels, 1, shape, 0.0});
         for (int lanes : {16, 32})
-            for (int stack : {1, 0}) c.push_back(Choice{lanes, levels, stack, 0.0});
+            for (int stack : {1, 0}) c.push_back(Choice{lanes, levels, stack, 0, 0.0});
     }
     return c;
 }
@@ -214,13 +223,14 @@ double ko_tune_measure(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoCh
     w.n_items = items;
     w.accs = d_acc;
     w.levels = n - 1 - d0 > 0 ? n - 1 - d0 : 1;
-    return time_candidate(fs, w, d_acc, 1, items * span, cand.lanes, cand.stack, ko_slab_bytes(h.S, h.Bk), reps, st);
+    return time_candidate(fs, w, d_acc, 1, items * span, cand.lanes, cand.stack, cand.shape, ko_slab_bytes(h.S, h.Bk),
+                          reps, st);
 }
 
 // Pick lanes / levels / node-state placement for the handle's set.
 ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAccum *d_acc,
                       const char *cache_path, cudaStream_t st, int *lanes_out, int *levels_out,
-                      int *stack_out, double *rate_out)
+                      int *stack_out, int *shape_out, double *rate_out)
 {
     const std::string key = key_of(h);
     std::map<std::string, Choice> cache = read_cache(cache_path);
@@ -229,6 +239,7 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAcc
         *lanes_out = it->second.lanes;
         *levels_out = it->second.levels;
         *stack_out = it->second.stack;
+        *shape_out = it->second.shape;
         *rate_out = it->second.rate;
         return KO_OK;
     }
@@ -255,6 +266,7 @@ ko_status ko_tune_set(KoFastState *fs, const KoSet &h, const KoSet *d_set, KoAcc
     *lanes_out = best.lanes;
     *levels_out = best.levels;
     *stack_out = best.stack;
+    *shape_out = best.shape;
     *rate_out = best.rate;
     return KO_OK;
 }
@@ -268,7 +280,7 @@ constexpr long long kBatchOrders = 1ll << 22;
 constexpr int kBatchSample = 64;
 
 ko_status ko_tune_batch(const KoSet *const *hs, int nsets, const char *cache_path, cudaStream_t st,
-                        int *lanes_out, int *levels_out, int *stack_out)
+                        int *lanes_out, int *levels_out, int *stack_out, int *shape_out)
 {
     std::map<std::string, std::vector<int>> classes;
     for (int i = 0; i < nsets; i++) classes["B_" + key_of(*hs[i])].push_back(i);
@@ -337,7 +349,7 @@ ko_status ko_tune_batch(const KoSet *const *hs, int nsets, const char *cache_pat
                 w.accs = d_accs;
                 w.levels = std::max(1, h0.n - 1 - d0);
                 const double r = time_candidate(&fs, w, d_accs, (int)sample.size(), orders, c.lanes, c.stack,
-                                                slab, warmed ? 1 : 2, st);
+                                                c.shape, slab, warmed ? 1 : 2, st);
                 warmed = true;
                 if (r > best.rate) {
                     best = c;
@@ -356,6 +368,7 @@ ko_status ko_tune_batch(const KoSet *const *hs, int nsets, const char *cache_pat
             lanes_out[i] = choice.lanes;
             levels_out[i] = choice.levels;
             stack_out[i] = choice.stack;
+            shape_out[i] = choice.shape;
         }
     }
     ko_fast_release(&fs);

@@ -333,6 +333,7 @@ def ko_eval_all(g, out, stream=None):
 
 
 KO_OPT_LANES, KO_OPT_LEVELS, KO_OPT_SIMPLE_ONLY, KO_OPT_RUN_LIMIT, KO_OPT_STACK_GLOBAL = 1, 2, 3, 4, 5
+KO_OPT_LANE_STATE = 6
 
 
 def ko_set_option(g, key, value):
@@ -721,7 +722,8 @@ class Gpu:
     def set_option(self, key, value):
         return ko_set_option(self.h, key, value)
 
-    def configure(self, lanes=None, levels=None, simple_only=None, run_limit=None, stack_global=None):
+    def configure(self, lanes=None, levels=None, simple_only=None, run_limit=None, stack_global=None,
+                  lane_state=None):
         if lanes is not None:
             self.set_option(KO_OPT_LANES, lanes)
         if levels is not None:
@@ -732,6 +734,8 @@ class Gpu:
             self.set_option(KO_OPT_RUN_LIMIT, run_limit)
         if stack_global is not None:
             self.set_option(KO_OPT_STACK_GLOBAL, int(bool(stack_global)))
+        if lane_state is not None:
+            self.set_option(KO_OPT_LANE_STATE, lane_state)
         return self
 
     def last_fallback_items(self):
@@ -741,7 +745,8 @@ class Gpu:
         ko_autotune(self.h, cache_path, stream)
         return {"lanes": ko_get_option(self.h, KO_OPT_LANES),
                 "levels": ko_get_option(self.h, KO_OPT_LEVELS),
-                "stack_global": ko_get_option(self.h, KO_OPT_STACK_GLOBAL)}
+                "stack_global": ko_get_option(self.h, KO_OPT_STACK_GLOBAL),
+                "lane_state": ko_get_option(self.h, KO_OPT_LANE_STATE)}
 
     def last_sim_ms(self):
         return ko_last_sim_ms(self.h)

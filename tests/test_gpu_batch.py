@@ -135,14 +135,14 @@ def test_batch_autotune_per_class(ko, tmp_path):
     by_class = {}
     for s, g in zip(sets, gpus):
         c = (ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
-             ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL))
-        assert c[0] in (1, 16, 32) and 1 <= c[1] <= min(s.n - 1, 5) and c[2] in (0, 1)
+             ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL), ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE))
+        assert c[0] in (1, 16, 32) and 1 <= c[1] <= min(s.n - 1, 5) and c[2] in (0, 1) and c[3] in (0, 1, 2)
         by_class.setdefault(_class_key(s), set()).add(c)
     assert all(len(v) == 1 for v in by_class.values())
     timed = {k for k in by_class if sum(math.factorial(s.n) for s in sets if _class_key(s) == k) >= 1 << 21}
     assert timed and timed <= set(data)
     for k in timed:
-        assert (data[k]["lanes"], data[k]["levels"], data[k]["stack"]) == next(iter(by_class[k]))
+        assert (data[k]["lanes"], data[k]["levels"], data[k]["stack"], data[k]["shape"]) == next(iter(by_class[k]))
     b = ko.Batch(gpus, nbins=0)
     res, _ = b.run()
     plain = [ko.Gpu.from_set(s) for s in sets]
@@ -161,4 +161,5 @@ def test_batch_autotune_per_class(ko, tmp_path):
     ko.ko_batch_autotune(again, cache)
     for s, g in zip(sets[:50], again):
         assert (ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
-                ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL)) == next(iter(by_class[_class_key(s)]))
+                ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL),
+                ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE)) == next(iter(by_class[_class_key(s)]))

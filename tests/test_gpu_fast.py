@@ -189,11 +189,11 @@ def test_autotune_choice_cache_and_exactness(ko, tmp_path):
     with ko.Gpu.from_set(s) as g:
         choice = g.autotune(cache)
         assert choice["lanes"] in (1, 16, 32) and 1 <= choice["levels"] <= 6
-        assert choice["stack_global"] in (0, 1)
+        assert choice["stack_global"] in (0, 1) and choice["lane_state"] in (0, 1, 2)
         assert np.array_equal(_all(g, 8), want)
     data = json.load(open(cache))
     assert data["S16_N8"]["lanes"] == choice["lanes"] and data["S16_N8"]["levels"] == choice["levels"]
-    assert data["S16_N8"]["stack"] == choice["stack_global"]
+    assert data["S16_N8"]["stack"] == choice["stack_global"] and data["S16_N8"]["shape"] == choice["lane_state"]
     with ko.Gpu.from_set(s) as g:   # second handle: served from the cache
         assert g.autotune(cache) == choice
 
