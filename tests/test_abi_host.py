@@ -98,6 +98,16 @@ def test_argument_validation(ko):
     with pytest.raises(ko.KoError):
         ko.ko_set_sampling(g.h, 2)
     ko.ko_set_sampling(g.h, ko.KO_SAMPLE_AT_PLACEMENT)
+    # tuning knobs: the one-thread simulator's three state sizes, nothing else
+    assert ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE) == 0
+    for v in (0, 1, 2):
+        ko.ko_set_option(g.h, ko.KO_OPT_LANE_STATE, v)
+        assert ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE) == v
+    for bad in (-1, 3):
+        with pytest.raises(ko.KoError):
+            ko.ko_set_option(g.h, ko.KO_OPT_LANE_STATE, bad)
+    with pytest.raises(ko.KoError):
+        ko.ko_set_option(g.h, ko.KO_OPT_LANES, 8)
     ko.ko_set_sampling(g.h, ko.KO_SAMPLE_BURST_END)
 
 
