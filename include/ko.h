@@ -384,7 +384,11 @@ ko_status ko_surrogate_search(ko_model *m, ko_gpu *g, int64_t n_cand, int32_t to
                               double *gpu_ms, void *stream);
 
 /* Plain random search, the baseline of the surrogate: n_orders uniform random
- * orders simulated exactly; the best one is returned. */
+ * orders simulated exactly; the best one is returned.  Like the exact
+ * rescoring of the surrogate calls and ko_local_search, it picks the threads
+ * per simulation by list length and N_SM (32 for more than 32 SMs or up to
+ * 4096 orders, 16 up to 32768, one thread per order beyond) instead of the
+ * handle's KO_OPT_LANES, which ko_eval_orders and the exhaustive calls use. */
 ko_status ko_random_search(ko_gpu *g, int64_t n_orders, uint64_t seed, int32_t *best_order,
                            int64_t *best_makespan, double *gpu_ms, void *stream);
 

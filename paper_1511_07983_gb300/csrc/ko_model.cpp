@@ -449,10 +449,29 @@ static ko_status build_tables(const KoSet *const *hs, int nsets, SetTables *tb, 
     return KO_OK;
 }
 
-// Exact makespans of `count` rows (stride 24) of set `set` into out.
+// Threads per simulation for `count` explicit orders of set h (measured on a
+// GB300 with 16- to 24-kernel sets): with more than 32 SMs the runs of
+// distinct SM states outgrow 16 lanes and the one-thread state, so 32 lanes;
+// otherwise 32 lanes up to 4096 orders (the latency of single simulations
+// decides), 16 up to 32768, one thread per order beyond.
+static int row_lanes(const KoSet &h, long long count)
+{
+    if (h.S > 32 || count <= 4096) return 32;
+    return count <= 32768 ? 16 : 1;
+}
+
+// Exact makespans of `count` rows (stride 24) of set `set` into out, with the
+// threads per simulation of row_lanes (the state's own choice is kept).
 static ko_status exact_rows(KoFastState *fs, const KoSet *d_sets, const KoSet &h, int set, const int8_t *rows,
                             long long count, int64_t *out, KoChunk *d_chunk, cudaStream_t st)
 {
+    struct Keep {  // restores the state's lanes and state size on every return
+        KoFastState *fs;
+        int lanes, shape;
+        ~Keep() { fs->lanes = lanes; fs->lane_shape = shape; }
+    } keep{fs, fs->lanes, fs->lane_shape};
+    fs->lanes = row_lanes(h, count);
+    fs->lane_shape = 0;
     KoChunk c{};
     c.count = count;
     c.set = set;
