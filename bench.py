@@ -3,7 +3,8 @@
 
 One step = the whole hot path through the public C ABI (ko_rank_order):
 Algorithm 1 order on the host, its makespan on the device, the makespan of all
-12! = 479,001,600 orders (run-length simulator, exact fallback included),
+12! = 479,001,600 orders (one-thread-per-order simulator; the run-length
+and simple simulators re-run the work items it cannot hold),
 min / max / better / equal / worse against the heuristic, and the 4096-bin
 histogram.  Inputs are seeded synthetic kernel sets (no dataset exists).
 
