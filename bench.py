@@ -508,14 +508,16 @@ def wins(a, b):
             "mean_gain": sum((y - x) / y for x, y in zip(a, b)) / len(a)}
 
 
-BATCH_WORKLOADS = {"sets10": (64, NBINS), "batched": (4096, 0)}
+BATCH_WORKLOADS = {"single8": (1, NBINS), "sets10": (64, NBINS), "batched": (4096, 0)}
 
 
 def run_batch(a):
     """Batched workloads: the 64 ten-kernel sets on a 15-SM GPU with 4096-bin
-    histograms, or the 4096 mixed sets (N 5..10 on 13/15/148-SM GPUs) with
-    per-set min / max / rank; one step = one replay of the batch's captured
-    graph (every order of every set), timed with CUDA events."""
+    histograms, the 4096 mixed sets (N 5..10 on 13/15/148-SM GPUs) with
+    per-set min / max / rank, or the one eight-kernel set on a 13-SM GPU
+    (40,320 orders, 4096-bin histogram; launch-latency-bound, run it with
+    --steps 100); one step = one replay of the batch's captured graph (every
+    order of every set), timed with CUDA events."""
     import torch
 
     from paper_1511_07983_gb300 import build, ko, synth
