@@ -532,7 +532,11 @@ def run_batch(a):
             g.configure(lanes=a.lanes, levels=a.levels)
     elif a.autotune:
         t0 = time.perf_counter()
-        ko.ko_batch_autotune(gpus, os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json"))
+        cache = os.path.join(ROOT, "paper_1511_07983_gb300", "ko_tune_cache.json")
+        if nsets == 1:
+            gpus[0].autotune(cache)   # one set: timed on its own space, as the step runs it
+        else:
+            ko.ko_batch_autotune(gpus, cache)
         choices = sorted({(ko.ko_get_option(g.h, ko.KO_OPT_LANES), ko.ko_get_option(g.h, ko.KO_OPT_LEVELS),
                            ko.ko_get_option(g.h, ko.KO_OPT_STACK_GLOBAL), ko.ko_get_option(g.h, ko.KO_OPT_LANE_STATE))
                           for g in gpus})

@@ -325,28 +325,48 @@ size_t slab_bytes(int levels)
     return sizeof(uint32_t) * (size_t)sms * lane_threads<SH>() * levels * SH::kSaveWords;
 }
 
+// Threads per block when a launch's work items cannot fill every SM with
+// full blocks: small blocks spread the items over all SMs, so each warp shares
+// its SM's issue slots with fewer warps (the simulation is latency-bound per
+// warp).
+constexpr int kSmallT = 64;
+
+template <int T, class SH>
+cudaError_t launch_lane_blocks(const KoWork &a, long long blocks, cudaStream_t st)
+{
+    const size_t smem = sizeof(uint32_t) * (size_t)SH::kWords * T;
+    cudaError_t e = cudaFuncSetAttribute(lane_kernel<T, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    lane_kernel<T, SH><<<(unsigned)blocks, T, smem, st>>>(a);
+    ko_count_launch();
+    return cudaGetLastError();
+}
+
 template <class SH>
 cudaError_t launch_lane(const KoWork &a, cudaStream_t st)
 {
     constexpr int T = lane_threads<SH>();
-    const size_t smem = sizeof(uint32_t) * (size_t)SH::kWords * T;
-    cudaError_t e = cudaFuncSetAttribute(lane_kernel<T, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int levels = a.levels < 1 ? 1 : a.levels;
+    const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
+    const long long needed = (work + T - 1) / T;
+    if (needed < sms && work > 0) {
+        // fewer items than SMs x T: blocks of kSmallT threads, one item per thread at most
+        long long blocks = (work + kSmallT - 1) / kSmallT;
+        const long long fit = a.gstack_words / ((long long)kSmallT * levels * SH::kSaveWords);
+        if (blocks > fit) blocks = fit;  // the slab holds sms x T threads' node states, so fit >= needed
+        if (blocks < 1) return cudaErrorInvalidValue;
+        return launch_lane_blocks<kSmallT, SH>(a, blocks, st);
+    }
     long long blocks = sms;
     const long long fit = a.gstack_words / ((long long)T * levels * SH::kSaveWords);
     if (blocks > fit) blocks = fit;
     if (blocks < 1) return cudaErrorInvalidValue;  // the slab holds no thread's node states
-    const long long work = a.item_list ? (long long)a.ov_cap : a.n_items;
-    const long long needed = (work + T - 1) / T;
     if (blocks > needed) blocks = needed;
     if (blocks < 1) blocks = 1;  // an empty list (a sizing launch): one block finds no work
-    lane_kernel<T, SH><<<(unsigned)blocks, T, smem, st>>>(a);
-    ko_count_launch();
-    return cudaGetLastError();
+    return launch_lane_blocks<T, SH>(a, blocks, st);
 }
 
 }  // namespace

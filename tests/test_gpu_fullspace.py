@@ -57,6 +57,8 @@ def _stats_equal(r, st):
         (st["n_better"], st["n_equal"], st["n_worse"])
 
 
+# (1, 3): 151,200 items, the one-thread pass in full blocks (one per SM); (1, 5): 5,040 items,
+# fewer than SMs x block threads, so it runs in the small blocks that spread them over the SMs
 @pytest.mark.parametrize("lanes,levels", [(None, None), (16, 4), (32, 3), (1, 3), (1, 5)])
 def test_n10_full_space(ko, n10, lanes, levels):
     import torch
