@@ -236,11 +236,15 @@ ko_batch *ko_batch_build(const KoSet *const *sets, const int *levels, const int 
         *err = KO_ERR_CUDA;
         return nullptr;
     }
-    // allocate the simulators' buffers outside capture: one empty launch per
-    // group, each with its choice, its deepest levels and the longest list
+    // allocate the simulators' buffers outside capture: one empty launch with
+    // the reference-order pass's choice (16 lanes, global slab, 1 level), then
+    // one per group, each with its choice, its deepest levels and the longest list
     long long longest = b->n_ref_items;
     for (const ko_batch::Group &gr : b->groups) longest = std::max(longest, gr.n_items);
-    for (const ko_batch::Group &gr : b->groups) {
+    std::vector<ko_batch::Group> sizing;
+    sizing.push_back(ko_batch::Group{16, 1, 0, 0, 0, 0, 1});
+    sizing.insert(sizing.end(), b->groups.begin(), b->groups.end());
+    for (const ko_batch::Group &gr : sizing) {
         KoWork none{};
         none.sets = b->d_sets;
         none.chunks = b->d_chunks;

@@ -49,6 +49,25 @@ def test_batch_small_sets_match_oracle(ko):
     assert b.orders() == sum(math.factorial(s.n) for s in sets)
 
 
+@pytest.mark.parametrize("lanes", [1, 16, 32])
+def test_batch_of_shared_memory_node_states(ko, lanes):
+    # every handle keeps its node states in shared memory: the graph's
+    # reference-order pass (global slab) must still have its slab sized
+    # before capture
+    sets = [s for s in (synth.gen_set("batched", i) for i in range(40)) if s.n <= 7][:8]
+    gpus = [ko.Gpu.from_set(s).configure(lanes=lanes, levels=2, stack_global=0) for s in sets]
+    b = ko.Batch(gpus, nbins=64)
+    res, hist = b.run()
+    for s, r, h in zip(sets, res, hist):
+        st = _oracle_stats(s, 64)
+        assert (r["min"], r["max"], r["makespan"]) == (st["min"], st["max"], st["makespan"])
+        assert (r["n_better"], r["n_equal"], r["n_worse"]) == (st["n_better"], st["n_equal"], st["n_worse"])
+        assert np.array_equal(h, st["hist"])
+    b.close()
+    for g in gpus:
+        g.close()
+
+
 def test_batch_equals_single_set_calls(ko):
     sets = [synth.gen_set("batched", i) for i in range(30, 46)]
     gpus = [ko.Gpu.from_set(s) for s in sets]
