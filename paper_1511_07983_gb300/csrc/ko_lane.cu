@@ -34,7 +34,7 @@ static_assert(lane_threads<ShapeL>() == 288 && lane_threads<ShapeM>() == 352 && 
               "simulations per SM of the three shapes");
 // Threads of a warp that must wait for the control step before it runs.
 #ifndef KO_LANE_GATHER
-#define KO_LANE_GATHER 16
+#define KO_LANE_GATHER 20
 #endif
 constexpr int kGather = KO_LANE_GATHER;
 
