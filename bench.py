@@ -198,6 +198,20 @@ def measured_counters(kernel, workload):
     return {k: f[k] for k in ("case", "issue_active_pct", "threads_per_inst", "warp_inst_per_order") if k in f}
 
 
+def executed_lane_ops(counters, orders, kernel_s, peak_gops):
+    """Integer lane-ops the dominant kernel executes, from its ncu counters
+    (warp instructions per order x active threads per instruction), as a rate
+    over the measured kernel time and as a fraction of the measured integer
+    peak; None without counters."""
+    if not counters or "warp_inst_per_order" not in counters or "threads_per_inst" not in counters:
+        return None
+    per_order = counters["warp_inst_per_order"] * counters["threads_per_inst"]
+    gops = per_order * orders / kernel_s / 1e9
+    return {"per_order": per_order, "achieved": gops, "frac": gops / peak_gops,
+            "from": f"ncu counters ({counters.get('case', '?')}): warp instructions per order x "
+                    f"threads per instruction"}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -353,6 +367,7 @@ def run_ours(a):
     achieved = placements * OPS_PER_PLACEMENT / kernel_s / 1e9
     kernel = "lane_kernel" if ko.ko_get_option(g.h, ko.KO_OPT_LANES) == 1 else "fast_kernel"
     traffic = measured_traffic(kernel, a.workload)
+    counters = measured_counters(kernel, a.workload)
     cb = cpu_baseline(kset, a.cpu_sample) if world == 1 else None
     sur = None
     if a.surrogate and world == 1:
@@ -383,7 +398,8 @@ def run_ours(a):
                      "peak_clocks": iclk_stats,
                      "issue_peak": issue_gops,
                      "issue_peak_from": f"{sm_count} SMs x 4 schedulers x 32 lanes x {max_mhz:.0f} MHz",
-                     "ncu": measured_counters(kernel, a.workload)},
+                     "ncu": counters,
+                     "ncu_lane_ops": executed_lane_ops(counters, n_orders, kernel_s, peak_gops)},
         "cpu_baseline": cb,
         "e2e": {"value": whole_job_rate(n_orders, a.steps, world, e2e_elapsed), "unit": "orders/s",
                 "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,

@@ -81,6 +81,16 @@ def test_traffic_figure_only_for_unchanged_kernel_sources(tmp_path, monkeypatch)
     assert bench.measured_counters("lane_kernel", "w") is None
 
 
+def test_executed_lane_ops_from_counters():
+    import bench
+    c = {"case": "n11", "warp_inst_per_order": 4000, "threads_per_inst": 8.0}
+    r = bench.executed_lane_ops(c, orders=1_000_000, kernel_s=2.0, peak_gops=32.0)
+    assert r["per_order"] == 32000.0
+    assert r["achieved"] == 16.0 and r["frac"] == 0.5
+    assert bench.executed_lane_ops(None, 1, 1.0, 1.0) is None
+    assert bench.executed_lane_ops({"threads_per_inst": 8.0}, 1, 1.0, 1.0) is None
+
+
 def test_reference_arm_line_on_rank0(monkeypatch, capsys):
     import json
     import bench
