@@ -215,7 +215,10 @@ ko_status ko_eval_all(ko_gpu *g, int64_t *makespans_out, void *stream);
  *                       (288 simulations per SM, default), 1 = 12 runs and
  *                       40 slots (352), 2 = 10 runs and 32 slots (448).
  *                       Smaller states fit more simulations on an SM; work
- *                       items that need more move on to the run-length passes
+ *                       items that need more move on to the run-length passes.
+ *                       A launch with fewer work items than SMs x those
+ *                       simulations runs in 64-thread blocks spread over
+ *                       every SM instead (one item per thread)
  * Results never depend on these knobs.  KO_ERR_ARG for an unknown key or
  * value. */
 #define KO_OPT_LANES 1
