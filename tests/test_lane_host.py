@@ -130,3 +130,21 @@ def test_single12_seeded_orders_and_a_subtree(harness):
     want = oracle.makespans_idx(s.gpu, s.kernels, first=_first_index(s.n, prefix), count=120)
     ok = got >= 0
     assert np.array_equal(got[ok], want[ok])
+
+
+def test_batched_workload_sets(harness):
+    # the mixed batch's sets (N 5..10 on 13-, 15- and 148-SM GPUs): whole spaces up to N = 7,
+    # a 120-order subtree above that
+    _, subtree = harness
+    seen = set()
+    for i in range(40):
+        s = synth.gen_set("batched", i)
+        prefix = [] if s.n <= 7 else list(range(s.n - 5))
+        count = math.factorial(s.n - len(prefix))
+        want = oracle.makespans_idx(s.gpu, s.kernels, first=_first_index(s.n, prefix), count=count)
+        got = subtree(s, prefix)
+        ok = got >= 0
+        assert ok.mean() > 0.9, i
+        assert np.array_equal(got[ok], want[ok]), i
+        seen.add(s.gpu[0])
+    assert seen == {13, 15, 148}
