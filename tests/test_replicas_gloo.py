@@ -104,3 +104,23 @@ def test_reference_arm_line_on_rank0(monkeypatch, capsys):
     assert line["metric"] == bench.METRIC and line["unit"] == "orders/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_algorithmic_placement_count_against_the_prefix_tree():
+    # the roofline's work unit: every distinct prefix places its last kernel's blocks once
+    import itertools
+    import bench
+    for n, blocks in ((1, [7]), (3, [1, 2, 3]), (5, [5, 1, 9, 2, 4])):
+        kernels = [[0, 0, 0, b, 0, 0] for b in blocks]
+        brute = sum(blocks[p[-1]] for d in range(1, n + 1) for p in itertools.permutations(range(n), d))
+        assert bench.placements_per_exhaustive(kernels) == brute
+
+
+def test_percentile_and_wins_helpers():
+    import numpy as np
+    import bench
+    ref = np.array([5, 6, 7, 8])
+    assert bench.percentile_of(6, ref) == 75.0 and bench.percentile_of(9, ref) == 0.0
+    w = bench.wins([1, 5, 3], [2, 5, 2])
+    assert (w["lower"], w["equal"], w["higher"]) == (1, 1, 1)
+    assert abs(w["mean_gain"] - ((2 - 1) / 2 + 0 + (2 - 3) / 2) / 3) < 1e-12
